@@ -1,0 +1,121 @@
+"""Pins for the oracle's precise algorithm (§III.B, Fig. 5, Eq. 10), double-count removal
+and the full pipeline against the image method."""
+import numpy as np
+import pytest
+
+from paper_2208_10009_gb300 import scenes
+
+
+def _ang(a, b):
+    return np.arctan2(np.linalg.norm(np.cross(a, b)), np.dot(a, b))
+
+
+def _dir(az, el):
+    return np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+
+
+@pytest.fixture(scope="module")
+def shoebox_run(oracle_mod):
+    sc, tx, rx = scenes.shoebox_config()
+    S = oracle_mod.Scene.from_generated(sc)
+    res = oracle_mod.sbr_pipeline(S, tx, rx, 64, 3, np.sqrt(3), 9, 5, refine_paths=False)
+    im = {p["faces"]: p for p in oracle_mod.image_enumerate(S, tx[0], rx[0], 3)}
+    return S, tx, rx, res, im
+
+
+def test_dedup_keeps_min_error(oracle_mod, shoebox_run):
+    S, tx, rx, res, im = shoebox_run
+    dirs = oracle_mod.lattice(64)
+    tr = oracle_mod.trace(S, tx[0], dirs, rx, 3, np.sqrt(3) * oracle_mod.theta_launch(64))
+    paths = oracle_mod.dedup(tr)
+    assert len(paths) == len({(r, tuple(f[:k])) for r, k, f in zip(tr.rec_rx, tr.rec_order, tr.rec_faces)})
+    for p in paths:
+        sel = [i for i in range(len(tr.rec_err)) if tr.rec_order[i] == p["order"]
+               and tuple(tr.rec_faces[i, :p["order"]]) == p["faces"]]
+        assert p["err"] == min(tr.rec_err[sel])
+        assert p["ray"] == min(tr.rec_ray[i] for i in sel if tr.rec_err[i] == p["err"])
+
+
+def test_shoebox_rough_paths_complete(shoebox_run):
+    """Every image-method path of the room (63 up to order 3) is found by the rough SBR."""
+    S, tx, rx, res, im = shoebox_run
+    assert sorted(p["faces"] for p in res.paths) == sorted(im)
+    assert res.nsegments == 4 * (10 * 64 * 64 + 2)
+
+
+def test_refinement_obeys_eq10_and_reaches_im(oracle_mod, shoebox_run):
+    """Eq. 10: after i iterations the error is <= R0 * shrink^i; the refined AOD is within
+    0.01 deg of the exact image-method AOD after 5 iterations with 9 sub-rays."""
+    S, tx, rx, res, im = shoebox_run
+    tl = oracle_mod.theta_launch(64)
+    _, _, s9 = oracle_mod.subray_pattern(9)
+    worst = 0.0
+    for p in res.paths:
+        R0 = max(tl, p["err"])
+        r = oracle_mod.refine(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 9, 5)
+        assert r["iters"] == 5
+        bound = R0 * s9 ** np.arange(6)
+        assert np.all(r["err_hist"] <= bound * (1 + 1e-9))
+        # Eq. 3 in unfolded space is exactly the angle to the exact AOD
+        e = _ang(r["dir"], im[p["faces"]]["aod_dir"])
+        assert abs(e - r["err"]) < 1e-12
+        worst = max(worst, e)
+    assert np.degrees(worst) < 0.01
+
+
+def test_refinement_k6_sixty_iterations_plateau(oracle_mod, shoebox_run):
+    """§IV, Fig. 8a: with the paper's six sub-rays the error stays under the Eq. 10 bound and
+    after ~60 iterations sits at the floating-point floor."""
+    S, tx, rx, res, im = shoebox_run
+    tl = oracle_mod.theta_launch(64)
+    s6 = 1 / np.sqrt(3)
+    for p in res.paths[::7]:
+        R0 = max(tl, p["err"])
+        r = oracle_mod.refine(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 6, 60)
+        h = r["err_hist"]
+        assert np.all(h[:40] <= R0 * s6 ** np.arange(40) * (1 + 1e-6) + 1e-15)
+        assert h[-1] < 1e-13
+        assert _ang(r["dir"], im[p["faces"]]["aod_dir"]) < 1e-13
+
+
+def test_early_stop_at_target(oracle_mod, shoebox_run):
+    S, tx, rx, res, im = shoebox_run
+    tl = oracle_mod.theta_launch(64)
+    target = np.radians(0.01)
+    for p in res.paths[:20]:
+        r = oracle_mod.refine(S, tx[0], rx[0], p["faces"], p["rough_dir"], max(tl, p["err"]), 9, 8, target)
+        assert r["err"] <= target
+        assert r["iters"] == 0 or r["err_hist"][-2] > target
+
+
+def test_pipeline_matches_image_method(oracle_mod, shoebox_run):
+    """After refinement and the validity test, the path set, delays and angles agree with
+    the image method (paths within 0.01 deg AOD; delay within the cone-error bound)."""
+    S, tx, rx, res, im = shoebox_run
+    out = oracle_mod.sbr_pipeline(S, tx, rx, 64, 3, np.sqrt(3), 9, 8)
+    assert all(p["valid"] for p in out.paths)
+    assert sorted(p["faces"] for p in out.paths) == sorted(im)
+    for p in out.paths:
+        q = oracle_mod.image_path(S, tx[0], rx[0], p["faces"])
+        assert np.degrees(_ang(_dir(*p["aod"]), q["aod_dir"])) < 0.01
+        assert np.degrees(_ang(_dir(*p["aoa"]), _dir(*q["aoa"]))) < 0.01
+        assert abs(p["delay"] / q["delay"] - 1) < 1e-6
+
+
+def test_brute_force_room_with_pillar(oracle_mod):
+    """Tiny scene with occlusion: a room with a pillar.  Refined SBR (n = 12) only returns
+    paths the exhaustive image method also finds valid, with matching delays, and finds
+    nearly all of them."""
+    b = scenes._Builder()
+    scenes.box_faces(b, (0, 0, 0), (6, 5, 3))
+    scenes.box_faces(b, (2.5, 2.0, 0.0), (3.5, 3.0, 3.0), bottom=False)
+    sc = b.finish()
+    S = oracle_mod.Scene.from_generated(sc)
+    tx, rx = np.array([[1.0, 1.0, 1.5]]), np.array([[5.0, 4.0, 1.2]])
+    im = {p["faces"]: p for p in oracle_mod.image_enumerate(S, tx[0], rx[0], 2)}
+    out = oracle_mod.sbr_pipeline(S, tx, rx, 12, 2, np.sqrt(3), 9, 40)
+    valid = {p["faces"]: p for p in out.paths if p["valid"]}
+    assert set(valid) <= set(im)
+    assert len(valid) >= 0.9 * len(im)
+    for f, p in valid.items():
+        assert abs(p["delay"] / im[f]["delay"] - 1) < 1e-9
