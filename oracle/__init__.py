@@ -360,8 +360,11 @@ def sbr_pipeline(scene: Scene, txs, rxs, n: int, max_order: int, alpha: float, K
                  refine_paths=True):
     """The whole hot path in the paper's order (Fig. 4): equiangular launch, brute-force
     trace with reception, double-count removal, the precise algorithm, then the validity
-    test and outputs.  The reception and initial refinement cone is alpha * theta_launch.
-    ``ray_ids`` restricts the launch to a subsample of the lattice."""
+    test and outputs.  The reception cone is alpha * theta_launch; the precise algorithm's
+    initial cone is the ray cone of Eq. 8, theta_launch, widened to the rough error angle
+    when that is larger (alpha > 1 can accept a ray outside its own cone), so the exact
+    direction is always inside it.  ``ray_ids`` restricts the launch to a subsample of the
+    lattice."""
     txs = _f64(txs, (-1, 3))
     rxs = _f64(rxs, (-1, 3))
     cone = alpha * theta_launch(n)
@@ -383,7 +386,8 @@ def sbr_pipeline(scene: Scene, txs, rxs, n: int, max_order: int, alpha: float, K
             c0 = lattice_ids(n, [p["ray"]])[0]
             p["rough_dir"] = c0
             if refine_paths:
-                r = refine(scene, tx, rxs[p["rx"]], p["faces"], c0, cone, K, iters, target)
+                R0 = max(theta_launch(n), p["err"])
+                r = refine(scene, tx, rxs[p["rx"]], p["faces"], c0, R0, K, iters, target)
                 p.update(ref_dir=r["dir"], ref_err=r["err"], iters=r["iters"], choice=r["choice"],
                          err_hist=r["err_hist"])
                 ev = path_eval(scene, tx, rxs[p["rx"]], p["faces"], r["dir"], freq)
