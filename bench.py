@@ -1,0 +1,379 @@
+"""Benchmark of the SBR hot path on the urban-canyon workload.
+
+Workload (seeded, synthetic): 20 x 20 box buildings + tessellated ground (~10k
+triangles), 1 Tx 25 m above the central intersection, 256 Rx on street intersections,
+equiangular division n = 700 (4,900,002 rays), up to 6 reflections, reception cone
+sqrt(3) * theta_launch, 6 refinement iterations with 9 sub-rays.  One step = ray
+generation + persistent trace with reception + double-count removal + batched
+refinement + validity test + outputs, replayed as one captured CUDA graph.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-bounces/s and refined paths/s at <=0.01 deg AOD/AOA error; % of roofline"
+WORKLOAD = dict(workload="urban canyon: 20x20 box city + ground (~10k tris), 1 Tx x 256 Rx, n=700, order 6, "
+                         "alpha=sqrt(3), 6 refinement iterations, K=9",
+                n_div=700, max_order=6, alpha=float(np.sqrt(3.0)), iters=6, K=9)
+ACC_DEG = 0.01
+# FLOPs per unit of the trace kernel (counted from the kernel source): slab test of a node's
+# two child boxes, one watertight triangle test, one receiver candidate test
+FLOP_NODE, FLOP_TRI, FLOP_RX = 24, 40, 20
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) == len(self.FIELDS):
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_sample(sc, tx, rx, stride, offset=0):
+    """The oracle (as it stands) on every `stride`-th ray of the workload: trace, dedup,
+    refinement, validity and outputs.  Returns (ray-bounces, refined paths, seconds)."""
+    import oracle
+    S = oracle.Scene.from_generated(sc)
+    n = WORKLOAD["n_div"]
+    ids = np.arange(offset, 10 * n * n + 2, stride, dtype=np.int64)
+    t0 = time.perf_counter()
+    res = oracle.sbr_pipeline(S, tx, rx, n, WORKLOAD["max_order"], WORKLOAD["alpha"], WORKLOAD["K"],
+                              WORKLOAD["iters"], ray_ids=ids)
+    dt = time.perf_counter() - t0
+    good = sum(1 for p in res.paths if p["valid"] and p["ref_err"] <= np.radians(ACC_DEG))
+    return res.nsegments, good, dt, len(ids), oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    from paper_2208_10009_gb300 import scenes
+    sc, tx, rx = scenes.urban_canyon()
+    stride = 4999
+    for w in range(args.warmup):
+        cpu_oracle_sample(sc, tx, rx, stride, offset=w)
+    segs = good = 0
+    secs = 0.0
+    nr = cores = 0
+    for k in range(args.steps):
+        s, g, dt, nrays, cores = cpu_oracle_sample(sc, tx, rx, stride, offset=args.warmup + k)
+        segs += s
+        good += g
+        secs += dt
+        nr += nrays
+    value = segs / secs
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ray-bounces/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {k: v for k, v in WORKLOAD.items()},
+           "cpu_baseline": {"value": value, "unit": "ray-bounces/s", "cores": cores, "kind": "oracle",
+                            "sample": f"every {stride}th ray id per step ({nr // max(args.steps, 1)} rays), "
+                                      f"brute-force FP64 trace + refine"},
+           "refined_paths_per_s": good / secs,
+           "e2e": {"value": value, "unit": "ray-bounces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2208_10009_gb300 import api, scenes
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc, tx, rx = scenes.urban_canyon()
+    n, order, alpha, iters, K = (WORKLOAD[k] for k in ("n_div", "max_order", "alpha", "iters", "K"))
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    ctx = api.Context(local, stream=stream)
+    scene = ctx.scene_from(sc)
+    rxs = ctx.rx_upload(rx)
+    tx_dev = torch.as_tensor(tx.astype(np.float32), device=dev)
+    # size the containers from one synchronous launch
+    probe = ctx.paths_create(1 << 20, 1 << 18)
+    ctx.launch(scene, tx_dev, rxs, probe, n, order, rx_angle_scale=alpha, sync=True)
+    st0 = ctx.launch_stats(probe)
+    probe.close()
+    paths = ctx.paths_create(max(2 * st0["records"], 1024), max(2 * st0["paths"], 256))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha)
+        ctx.batch_refine(scene, paths, iters, K)
+
+    # one timed (event) launch to split the step into kernels
+    for _ in range(2):
+        step()
+    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.batch_refine(scene, paths, iters, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st_t = ctx.launch_stats(paths)
+    ms_refine = e0.elapsed_time(e1)
+
+    # capture the whole step as one CUDA graph
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream, capture_error_mode="thread_local"):
+        step()
+    for _ in range(args.warmup):
+        flush.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            graph.replay()
+            b.record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    st = ctx.launch_stats(paths)
+    recs = ctx.query(paths)
+
+    # accuracy: Eq. 3 error angle of the refined launch = AOD error; AOA compared with the
+    # exact fixed-face-sequence AOA from the unfolding kernel
+    good = _count_accurate(ctx, scene, tx, rx, recs)
+    bounces = st["segments"] * world
+    secs = ms / 1e3
+    value = bounces * args.steps / secs
+    # roofline of the dominant kernel (trace): algorithmic FP32 FLOPs / its event time
+    flops = FLOP_NODE * st_t["node_visits"] + FLOP_TRI * st_t["tri_tests"] + FLOP_RX * st_t["rx_tests"]
+    peaks, src = _peaks()
+    sms = ctx.num_sms
+    peak_tflops = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (st_t["ms_trace"] / 1e3) / 1e12
+
+    # the batched graph form vs the plain per-pair launch-and-refine form
+    per_pair_ms = _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, len(rx))
+    batch_ms = _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream)
+
+    e2e = _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args)
+
+    out = {"metric": METRIC, "value": value, "unit": "ray-bounces/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32 (f64 in final refinement iterations)", "data": "synthetic",
+           "config": dict(WORKLOAD, triangles=int(sc.nt), rays=int(10 * n * n + 2), l2="flushed (256 MiB write) "
+                          "between timed steps, outside the event-timed region", parallelism="replicas" if world > 1
+                          else "single GPU"),
+           "refined_paths_per_s": good * args.steps / secs,
+           "refined_paths_accurate": good, "paths": int(len(recs)),
+           "valid_paths": int(np.sum(recs["valid"] == 1)),
+           "ray_bounces_per_step": int(st["segments"]),
+           "kernel_ms": {"raygen": st_t["ms_raygen"], "trace": st_t["ms_trace"], "dedup": st_t["ms_dedup"],
+                         "batch_refine": ms_refine},
+           "trace_counters": {k: st_t[k] for k in ("node_visits", "tri_tests", "rx_tests", "records", "segments")},
+           "refine_batched_graph_ms": batch_ms, "refine_per_pair_ms": per_pair_ms,
+           "roofline": {"bound": "alu", "kernel": "trace_kernel", "achieved": achieved, "peak": peak_tflops,
+                        "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                        "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} MEASURED_PEAKS.json)",
+                        "flops_per_launch": flops},
+           "clocks": clocks, "gpu_launches": 6 * args.steps, "wall_s": t_wall, "e2e": e2e}
+    if rank == 0 and not args.no_cpu_baseline:
+        s, g, dt, nr, cores = cpu_oracle_sample(sc, tx, rx, 997)
+        out["cpu_baseline"] = {"value": s / dt, "unit": "ray-bounces/s", "cores": cores, "kind": "oracle",
+                               "sample": f"every 997th ray id ({nr} rays): brute-force FP64 trace, dedup, refine, "
+                                         f"validity; {dt:.1f} s", "refined_paths_per_s": g / dt}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    for h in (paths, rxs, scene):
+        h.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _count_accurate(ctx, scene, tx, rx, recs):
+    import torch
+    if len(recs) == 0:
+        return 0
+    v = recs[recs["valid"] == 1]
+    dev = "cuda"
+    T = torch.as_tensor(np.asarray(tx, np.float32)[v["tx"]], device=dev)
+    R = torch.as_tensor(np.asarray(rx, np.float32)[v["rx"]], device=dev)
+    d = v["dir"]
+    ae = np.stack([np.arctan2(d[:, 1], d[:, 0]), np.arctan2(d[:, 2], np.hypot(d[:, 0], d[:, 1]))], -1)
+    AE = torch.as_tensor(ae.astype(np.float32), device=dev)
+    F = torch.as_tensor(v["faces"].astype(np.int32), device=dev)
+    O = torch.as_tensor(v["order"].astype(np.int32), device=dev)
+    out = ctx.unfold_fwd(scene, T, R, AE, F, O).cpu().numpy().astype(np.float64)
+
+    def unit(az, el):
+        return np.stack([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)], -1)
+
+    a = unit(v["aoa"][:, 0].astype(np.float64), v["aoa"][:, 1].astype(np.float64))
+    b = unit(out[:, 6], out[:, 7])
+    aoa_err = np.arctan2(np.linalg.norm(np.cross(a, b), axis=1), np.sum(a * b, axis=1))
+    ok = (v["err"] <= np.radians(ACC_DEG)) & (aoa_err <= np.radians(ACC_DEG))
+    return int(ok.sum())
+
+
+def _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, nrx):
+    import torch
+    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+    ctx.refine_pair(scene, paths, 0, 0, iters, K)   # builds the pair buckets
+    torch.cuda.synchronize()
+    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+    t = time.perf_counter()
+    for r in range(nrx):
+        ctx.refine_pair(scene, paths, 0, r, iters, K)
+    torch.cuda.synchronize()
+    return 1e3 * (time.perf_counter() - t)
+
+
+def _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream):
+    import torch
+    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+        ctx.batch_refine(scene, paths, iters, K)
+    g.replay()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    g.replay()
+    torch.cuda.synchronize()
+    return 1e3 * (time.perf_counter() - t)
+
+
+def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args):
+    """Same step through the C ABI with host inputs: Tx/Rx from pinned host memory (the
+    receiver BVH is rebuilt from them), results read back to pinned host memory."""
+    import torch
+
+    from paper_2208_10009_gb300 import _binding as B
+    tx_h = torch.as_tensor(np.asarray(tx, np.float32)).pin_memory().numpy()
+    rx_h = torch.as_tensor(np.asarray(rx, np.float32)).pin_memory().numpy()
+    out_h = torch.empty(paths.path_cap * 128, dtype=torch.uint8).pin_memory().numpy().view(B.PATH_DTYPE)
+    nbytes_out = 0
+
+    def one():
+        nonlocal nbytes_out
+        rxs = ctx.rx_upload(rx_h)
+        ctx.launch(scene, tx_h, rxs, paths, n, order, rx_angle_scale=alpha)
+        ctx.batch_refine(scene, paths, iters, K)
+        got = ctx.query(paths, out_h)
+        nbytes_out = len(got) * 128
+        rxs.close()
+        return ctx.launch_stats(paths)["segments"]
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    segs = 0
+    for _ in range(args.steps):
+        segs += one()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t
+    return {"value": segs / dt, "unit": "ray-bounces/s", "h2d_bytes_per_step": int(tx_h.nbytes + rx_h.nbytes),
+            "d2h_bytes_per_step": int(nbytes_out), "note": "h2d counts the Tx/Rx coordinates handed over; the "
+            "receiver BVH built from them is uploaded too"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

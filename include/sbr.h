@@ -1,0 +1,266 @@
+/*
+ * sbr.h -- C ABI of the GB300 shooting-and-bouncing-ray (SBR) library.
+ *
+ * The library implements the hot path of Zhou et al., "An Improved Equiangular Division
+ * Algorithm for SBR based Ray Tracing Channel Modeling" (arXiv 2208.10009):
+ *   equiangular ray launching (§II.B, Eq. 1-2), tracing with specular reflection and the
+ *   reception judgment (§III.A, Fig. 4, Eq. 3), double-count removal (§III.A), the
+ *   iterative precise algorithm (§III.B, Fig. 5, Eq. 10), the validity test (§III.A) and
+ *   the channel outputs delay / AOD / AOA / power (§IV), plus a batched persistent
+ *   refinement and the adjoint of the fixed-face-sequence unfolding.
+ *
+ * Conventions (every entry point):
+ *   - Returns sbr_status; SBR_OK == 0.  On error, sbr_last_error(ctx) holds a message.
+ *     No C++ exception crosses this boundary.
+ *   - All GPU work is enqueued on the context's stream (sbr_ctx_create /
+ *     sbr_ctx_set_stream) and is asynchronous unless the entry point says it
+ *     synchronises.
+ *   - Host input arrays are copied before the call returns; the caller keeps ownership.
+ *     Pointers documented "host or device" are classified with cudaPointerGetAttributes.
+ *   - Device memory owned by handles is obtained through the context's allocator
+ *     callbacks (or cudaMallocAsync when none are given) and released by the matching
+ *     destroy call.
+ *   - Coordinates are metres in a right-handed frame; angles are radians; azimuth =
+ *     atan2(y, x) in (-pi, pi], elevation = atan2(z, hypot(x, y)).
+ *   - A "face" is a planar polygon given as triangles sharing a face id; path face
+ *     sequences name faces.  At most SBR_MAX_ORDER reflections per path.
+ */
+#ifndef SBR_H_
+#define SBR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBR_ABI_VERSION 1
+#define SBR_MAX_ORDER 8
+
+typedef enum {
+    SBR_OK = 0,
+    SBR_EINVAL = 1,      /* bad argument (null handle, size out of range, unknown K...) */
+    SBR_ENOMEM = 2,      /* device or host allocation failed */
+    SBR_ECUDA = 3,       /* a CUDA runtime call failed (message has the CUDA error) */
+    SBR_ETIMEOUT = 4,    /* a bounded device-side wait gave up (persistent queue) */
+    SBR_EOVERFLOW = 5,   /* a record or path buffer was too small; counts say how large */
+    SBR_EDEGENERATE = 6, /* scene has NaN/Inf vertices, zero-area triangles or bad ids */
+    SBR_ECOLLISION = 7   /* two different face sequences shared a 64-bit dedup hash */
+} sbr_status;
+
+typedef struct sbr_ctx sbr_ctx;
+typedef struct sbr_scene sbr_scene;
+typedef struct sbr_rxset sbr_rxset;
+typedef struct sbr_paths sbr_paths;
+
+/* Allocator callbacks: return a device pointer of at least `bytes` bytes usable on
+ * `stream` (NULL on failure); free releases it.  `user` is passed through. */
+typedef void *(*sbr_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*sbr_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on CUDA device `device` that enqueues work on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  alloc/free may both be NULL
+ * (cudaMallocAsync / cudaFreeAsync on the stream are used then). */
+sbr_status sbr_ctx_create(int device, void *stream, sbr_alloc_fn alloc, sbr_free_fn free_fn, void *user,
+                          sbr_ctx **out);
+sbr_status sbr_ctx_destroy(sbr_ctx *ctx);
+sbr_status sbr_ctx_set_stream(sbr_ctx *ctx, void *stream);
+/* Message of the last failed call on this context ("" if none).  Valid until the next call. */
+const char *sbr_last_error(const sbr_ctx *ctx);
+const char *sbr_status_string(sbr_status s);
+int32_t sbr_abi_version(void);
+/* Number of SMs of the context's device (for grid sizing by callers). */
+int32_t sbr_ctx_num_sms(const sbr_ctx *ctx);
+
+/* ---------------------------------------------------------------- launch geometry */
+/* §III.B: rays launched at division level n (edges of the icosahedron split into n
+ * equal angles): N = 10 n^2 + 2.  Returns -1 for n < 1. */
+int64_t sbr_num_rays(int32_t n_div);
+/* Eq. 8: cone half-angle theta_launch = theta_0 / (sqrt(3) n), theta_0 = acos(1/sqrt(5)). */
+double sbr_theta_launch(int32_t n_div);
+/* Sub-ray pattern of the precise algorithm (§III.B, Fig. 5) for K in {6, 7, 9, 16}:
+ * ring radius rho[k] and azimuth phi[k] of each sub-ray, as a fraction of the cone
+ * half-angle and in radians, and the per-iteration shrink factor.  rho and phi must
+ * hold K doubles (host).  K = 6 is the paper's pattern (shrink 1/sqrt(3)). */
+sbr_status sbr_subray_pattern(int32_t K, double *rho, double *phi, double *shrink);
+
+/* a1 -- §II.B, Eq. 1-2: equiangular division of the regular icosahedron.  Writes the
+ * N = 10 n^2 + 2 unit launch directions as float4 (x, y, z, 0) to the DEVICE buffer
+ * `dirs` (capacity cap_rays rows).  Order: 12 icosahedron vertices; 30 edges x (n-1)
+ * equal-angle points (lower to higher vertex id); then per face its interior points by
+ * layer a = 1, 2, ... (3(n - 3a) points each) and, when n = 0 mod 3, the face centre.
+ * SBR_EINVAL if n < 1 or n > 20000; SBR_EOVERFLOW if cap_rays < N. */
+sbr_status sbr_raygen(sbr_ctx *ctx, int32_t n_div, float *dirs, int64_t cap_rays);
+
+/* ---------------------------------------------------------------- scene */
+typedef struct {
+    int64_t num_triangles;
+    int32_t num_faces;
+    int32_t bvh_nodes;
+    int32_t bvh_depth;
+    int32_t max_leaf;
+    int64_t device_bytes;
+    float bbox_lo[3], bbox_hi[3];
+} sbr_scene_info;
+
+/* Upload a triangle scene and build its SAH BVH on the host.  verts: nv x 3 floats;
+ * tris: nt x 3 vertex ids; tri_face: nt face ids in [0, nf); face_eps: nf relative
+ * permittivities (NULL or values <= 0: perfect reflector).  All host pointers.  A face's
+ * plane is taken from its first triangle.  SBR_EDEGENERATE for NaN/Inf vertices, ids
+ * out of range or zero-area triangles. */
+sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const int32_t *tris,
+                            const int32_t *tri_face, int64_t nt, const float *face_eps, int32_t nf,
+                            sbr_scene **out);
+sbr_status sbr_scene_destroy(sbr_ctx *ctx, sbr_scene *scene);
+sbr_status sbr_scene_get_info(const sbr_scene *scene, sbr_scene_info *out);
+
+/* ---------------------------------------------------------------- receivers */
+/* Upload nrx receiver positions (host, nrx x 3 floats) and build their BVH (used by the
+ * reception judgment to find candidate Rx near a ray segment). */
+sbr_status sbr_rx_upload(sbr_ctx *ctx, const float *rx, int32_t nrx, sbr_rxset **out);
+sbr_status sbr_rx_destroy(sbr_ctx *ctx, sbr_rxset *rx);
+
+/* ---------------------------------------------------------------- paths */
+/* Device container for reception records and paths.  record_cap bounds the records one
+ * launch may emit (before double-count removal), path_cap the unique paths. */
+sbr_status sbr_paths_create(sbr_ctx *ctx, int64_t record_cap, int64_t path_cap, sbr_paths **out);
+sbr_status sbr_paths_destroy(sbr_ctx *ctx, sbr_paths *paths);
+
+typedef struct {
+    int32_t n_div;           /* division level n >= 1 */
+    int32_t max_order;       /* maximum reflections, 0..SBR_MAX_ORDER */
+    float rx_angle_scale;    /* alpha: reception cone = alpha * theta_launch (1 = paper) */
+    int32_t flags;           /* SBR_LAUNCH_* */
+    int32_t dump_stride;     /* > 0: record per-ray face sequences of ray ids % stride == 0 */
+    int32_t *dump_faces;     /* device, [ntx][ceil(N/stride)][max_order+1] face per segment
+                                (-1 miss, -2 not traced), or NULL */
+    int64_t dump_cap;        /* int32 entries in dump_faces; SBR_EINVAL if too small */
+    int32_t grid_blocks;     /* persistent trace grid (0 = one wave over all SMs) */
+    int32_t block_threads;   /* 0 = default (128) */
+} sbr_launch_params;
+
+#define SBR_LAUNCH_SYNC 1    /* synchronise at the end and report overflow / collisions */
+#define SBR_LAUNCH_TIMING 2  /* record CUDA events around each kernel (read by get_stats) */
+
+typedef struct {
+    int64_t rays;            /* rays traced (ntx * N) */
+    int64_t segments;        /* closest-hit queries = ray-bounces */
+    int64_t node_visits;     /* BVH inner nodes visited */
+    int64_t tri_tests;       /* ray-triangle tests */
+    int64_t rx_tests;        /* candidate Rx tested */
+    int64_t records;         /* reception records emitted (may exceed record_cap) */
+    int64_t paths;           /* unique paths after double-count removal (may exceed path_cap) */
+    int64_t collisions;      /* dedup hash collisions detected (must be 0) */
+    int32_t ntx, nrx, n_div, max_order;
+    float ms_raygen, ms_trace, ms_dedup; /* device time of each kernel group (SBR_LAUNCH_TIMING), else 0 */
+    int32_t trace_grid, trace_block;     /* launch shape of the trace kernel */
+} sbr_launch_stats;
+
+/* a1-a5 -- §III.A / Fig. 4: launch N rays from each of ntx transmitters (tx: ntx x 3
+ * floats, host or device), trace up to max_order specular reflections through the
+ * scene's BVH (closest hit, watertight triangle test), run the reception judgment
+ * against every receiver on every segment (Rx inside the cone alpha * theta_launch,
+ * error angle Eq. 3) and remove double counts (per (Tx, Rx, face sequence) keep the
+ * smallest error angle, ties to the lowest ray id).  The paths replace the container's
+ * previous contents.  Asynchronous unless SBR_LAUNCH_SYNC; overflow is reported by
+ * sbr_launch_get_stats (and by the SYNC return code). */
+sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int32_t ntx,
+                      const sbr_rxset *rx, const sbr_launch_params *params, sbr_paths *paths);
+/* Synchronises the stream and reads the counters of the container's last launch. */
+sbr_status sbr_launch_get_stats(sbr_ctx *ctx, const sbr_paths *paths, sbr_launch_stats *out);
+
+/* ---------------------------------------------------------------- refinement */
+typedef struct {
+    int32_t max_iters;       /* iteration cap (>= 0) */
+    int32_t subrays;         /* K in {6, 7, 9, 16} */
+    double target_err_rad;   /* stop once the error angle is <= this (<= 0: never early) */
+    double fp64_below_rad;   /* run an iteration in FP64 once the cone half-angle is below
+                                this (default 1e-5 when 0) */
+    double freq_hz;          /* carrier for the power term (0: 2.4e9) */
+    double ptx_dbm;          /* transmit power */
+    int8_t *choice_log;      /* device [path_cap][max_iters] argmin sub-ray per iteration, or NULL */
+} sbr_refine_params;
+
+/* a6-a8 -- §III.B, Fig. 5, Eq. 10 and §III.A: refine every path of the container.  The
+ * initial cone is centred on the path's rough launch direction with half-angle
+ * max(theta_launch, rough error angle); each iteration traces K sub-rays through the
+ * path's fixed face planes, keeps the one with the smallest error angle (Eq. 3) and
+ * shrinks the cone.  Then the validity test (bounce points inside their faces, no
+ * segment occluded) and the outputs (delay, AOD, AOA, power).  One thread per path,
+ * static schedule. */
+sbr_status sbr_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths, const sbr_refine_params *params);
+/* Same as sbr_refine restricted to the paths of one (tx, rx) pair: the per-pair form. */
+sbr_status sbr_refine_pair(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths, int32_t tx, int32_t rx,
+                           const sbr_refine_params *params);
+
+typedef struct {
+    int32_t block_threads;   /* threads per block (0 = 128) */
+    int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid (0 = max) */
+    int32_t chunk;           /* paths a warp takes from the queue per grab (0 = 32) */
+} sbr_batch_config;
+
+/* a9 -- batched form of a6-a8: one persistent launch refines all paths of all (Tx, Rx)
+ * pairs; warps take chunks of paths from a device work queue (atomic head), so paths
+ * that stop early (target reached) free their lanes for new ones.  Capturable in a CUDA
+ * graph (no host synchronisation, no allocation after the first call per container). */
+sbr_status sbr_batch_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths,
+                            const sbr_refine_params *params, const sbr_batch_config *cfg);
+
+/* ---------------------------------------------------------------- results */
+typedef struct {
+    int32_t tx, rx;          /* transmitter / receiver index */
+    int32_t ray;             /* lattice ray id of the rough path */
+    int32_t order;           /* reflections */
+    int32_t faces[SBR_MAX_ORDER]; /* face sequence, -1 padded */
+    float rough_err;         /* Eq. 3 error angle of the rough path (rad) */
+    float rough_dray;        /* propagation distance to the foot of Rx (m) */
+    int32_t iters;           /* refinement iterations done */
+    int32_t valid;           /* 1 if the validity test passed (after refinement) */
+    double dir[3];           /* launch direction (refined if iters > 0) */
+    double err;              /* Eq. 3 error angle of dir (rad) */
+    double delay;            /* s */
+    float aod[2];            /* azimuth, elevation of departure */
+    float aoa[2];            /* azimuth, elevation of p_k - Rx (Tx - Rx for LOS) */
+    float power_dbm;
+    int32_t flags;           /* SBR_PATH_* */
+} sbr_path_record;           /* 128 bytes */
+
+#define SBR_PATH_REFINED 1
+#define SBR_PATH_FP64 2      /* at least one iteration ran in FP64 */
+#define SBR_PATH_TRACE_FAIL 4 /* all sub-rays invalid at some iteration */
+
+/* Number of paths in the container (synchronises). */
+sbr_status sbr_paths_count(sbr_ctx *ctx, const sbr_paths *paths, int64_t *out);
+/* Copy up to cap path records to `out` (host or device); *written = records copied.
+ * Synchronises.  Record order is unspecified (sort by tx, rx, order, faces). */
+sbr_status sbr_query(sbr_ctx *ctx, const sbr_paths *paths, sbr_path_record *out, int64_t cap, int64_t *written);
+/* Replace the container's paths with `count` records (host or device), e.g. to resume
+ * refinement from exported rough paths.  tx/rx positions are taken from `tx` (ntx x 3,
+ * host or device) and the receiver set. */
+sbr_status sbr_paths_import(sbr_ctx *ctx, sbr_paths *paths, const sbr_path_record *in, int64_t count,
+                            const float *tx, int32_t ntx, const sbr_rxset *rx, int32_t n_div);
+
+/* ---------------------------------------------------------------- unfolding + adjoint */
+/* a10 -- fixed-face-sequence unfolding (the exact per-sequence geometry that the precise
+ * algorithm converges to).  For path p with faces[p*8 .. p*8+order[p]) and mirror maps
+ * M_f(x) = x - 2 (n.x - h) n: Rx' = M_f1(...M_fk(Rx)), w = Rx' - Tx, d = launch direction
+ * of (az, el).  Outputs per path (8 floats): miss[3] = real-space vector from the foot of
+ * Rx on the last leg to Rx, delay = |w| / c0, AOD (az, el) of w, AOA (az, el) of the last
+ * Tx image minus Rx.  All pointers DEVICE: tx, rx [P][3]; az_el [P][2]; faces [P][8];
+ * order [P]; out [P][8]. */
+sbr_status sbr_unfold_fwd(sbr_ctx *ctx, const sbr_scene *scene, int64_t npaths, const float *tx,
+                          const float *rx, const float *az_el, const int32_t *faces, const int32_t *order,
+                          float *out);
+/* Vector-Jacobian product of sbr_unfold_fwd: given grad_out [P][8], writes grad_tx,
+ * grad_rx [P][3] and grad_az_el [P][2] (DEVICE).  Bounce state is recomputed, not read
+ * from the forward pass. */
+sbr_status sbr_unfold_bwd(sbr_ctx *ctx, const sbr_scene *scene, int64_t npaths, const float *tx,
+                          const float *rx, const float *az_el, const int32_t *faces, const int32_t *order,
+                          const float *grad_out, float *grad_tx, float *grad_rx, float *grad_az_el);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBR_H_ */

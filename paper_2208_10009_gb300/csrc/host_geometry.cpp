@@ -1,0 +1,333 @@
+// host_geometry.cpp -- host-side construction for the CUDA path: binned-SAH BVH, the
+// equiangular lattice's layer tables (§II.B, Eq. 1-2) and the precise algorithm's
+// sub-ray patterns (§III.B, Fig. 5).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "sbr_internal.h"
+
+namespace sbr {
+
+// ============================================================================ BVH
+namespace {
+
+struct Box {
+    float lo[3] = {INFINITY, INFINITY, INFINITY};
+    float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    void grow(const float *l, const float *h) {
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], l[a]);
+            hi[a] = std::max(hi[a], h[a]);
+        }
+    }
+    void grow(const Box &b) { grow(b.lo, b.hi); }
+    float area() const {
+        if (!(hi[0] >= lo[0])) return 0.0f;
+        float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+        return 2.0f * (dx * dy + dy * dz + dz * dx);
+    }
+};
+
+struct TmpNode {
+    Box box;
+    int left = -1, right = -1;   // children (TmpNode ids) or -1 for a leaf
+    int first = 0, count = 0;
+};
+
+struct Builder {
+    const std::vector<float> &lo, &hi;
+    std::vector<float> cen;
+    std::vector<int> idx;
+    std::vector<TmpNode> nodes;
+    int leaf_max;
+    int depth = 0, max_leaf = 0;
+
+    Builder(const std::vector<float> &l, const std::vector<float> &h, int lm) : lo(l), hi(h), leaf_max(lm) {
+        size_t n = l.size() / 3;
+        cen.resize(3 * n);
+        for (size_t i = 0; i < 3 * n; ++i) cen[i] = 0.5f * (l[i] + h[i]);
+        idx.resize(n);
+        std::iota(idx.begin(), idx.end(), 0);
+    }
+
+    int make(int first, int count, int d) {
+        depth = std::max(depth, d);
+        int id = (int)nodes.size();
+        nodes.emplace_back();
+        Box b, cb;
+        for (int i = first; i < first + count; ++i) {
+            int p = idx[i];
+            b.grow(&lo[3 * p], &hi[3 * p]);
+            cb.grow(&cen[3 * p], &cen[3 * p]);
+        }
+        nodes[id].box = b;
+        nodes[id].first = first;
+        nodes[id].count = count;
+        if (count <= leaf_max || d >= kStackDepth - 8) {
+            max_leaf = std::max(max_leaf, count);
+            return id;
+        }
+        // binned SAH over the centroid bounds
+        const int B = 32;
+        float best_cost = INFINITY;
+        int best_axis = -1, best_split = 0;
+        for (int a = 0; a < 3; ++a) {
+            float ext = cb.hi[a] - cb.lo[a];
+            if (!(ext > 0.0f)) continue;
+            Box bins[B];
+            int cnt[B] = {0};
+            float scale = B / ext;
+            for (int i = first; i < first + count; ++i) {
+                int p = idx[i];
+                int k = std::min(B - 1, (int)((cen[3 * p + a] - cb.lo[a]) * scale));
+                bins[k].grow(&lo[3 * p], &hi[3 * p]);
+                ++cnt[k];
+            }
+            float right_area[B];
+            int right_cnt[B];
+            Box acc;
+            int c = 0;
+            for (int k = B - 1; k > 0; --k) {
+                acc.grow(bins[k]);
+                c += cnt[k];
+                right_area[k] = acc.area();
+                right_cnt[k] = c;
+            }
+            Box lacc;
+            int lc = 0;
+            for (int k = 1; k < B; ++k) {
+                lacc.grow(bins[k - 1]);
+                lc += cnt[k - 1];
+                if (lc == 0 || right_cnt[k] == 0) continue;
+                float cost = lacc.area() * lc + right_area[k] * right_cnt[k];
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_axis = a;
+                    best_split = k;
+                }
+            }
+        }
+        int mid;
+        if (best_axis < 0) {
+            // all centroids coincide: split the range in half
+            mid = first + count / 2;
+        } else {
+            float leaf_cost = b.area() * count;
+            float inner_cost = 0.125f * b.area() + best_cost;  // traversal cost ~ 1/8 triangle
+            if (inner_cost >= leaf_cost && count <= 2 * leaf_max) {
+                max_leaf = std::max(max_leaf, count);
+                return id;
+            }
+            float ext = cb.hi[best_axis] - cb.lo[best_axis];
+            float scale = B / ext;
+            auto it = std::partition(idx.begin() + first, idx.begin() + first + count, [&](int p) {
+                int k = std::min(B - 1, (int)((cen[3 * p + best_axis] - cb.lo[best_axis]) * scale));
+                return k < best_split;
+            });
+            mid = (int)(it - idx.begin());
+            if (mid == first || mid == first + count) mid = first + count / 2;
+        }
+        int l = make(first, mid - first, d + 1);
+        int r = make(mid, first + count - mid, d + 1);
+        nodes[id].left = l;
+        nodes[id].right = r;
+        return id;
+    }
+};
+
+void put_child(float4 *n, int slot, const Box &b) {
+    float *f = reinterpret_cast<float *>(n);
+    int o = slot == 0 ? 0 : 6;
+    if (!(b.hi[0] >= b.lo[0])) {
+        // empty child: a point far outside any scene (its leaf has no primitives)
+        for (int a = 0; a < 6; ++a) f[o + a] = 1e30f;
+        return;
+    }
+    f[o + 0] = b.lo[0]; f[o + 1] = b.lo[1]; f[o + 2] = b.lo[2];
+    f[o + 3] = b.hi[0]; f[o + 4] = b.hi[1]; f[o + 5] = b.hi[2];
+}
+
+}  // namespace
+
+bool build_bvh(const std::vector<float> &lo, const std::vector<float> &hi, int leaf_max, BvhOut &out,
+               std::string &err) {
+    size_t n = lo.size() / 3;
+    if (n >= (1u << 24)) {
+        err = "BVH: more than 2^24 primitives";
+        return false;
+    }
+    Builder b(lo, hi, leaf_max);
+    if (n > 0) b.make(0, (int)n, 1);
+    // Flatten: every inner TmpNode becomes one 64-byte node holding its children.
+    std::vector<int> flat_id(b.nodes.size(), -1);
+    std::vector<int> order;   // TmpNode ids of inner nodes, preorder
+    std::vector<int> stack;
+    if (!b.nodes.empty() && b.nodes[0].left >= 0) stack.push_back(0);
+    while (!stack.empty()) {
+        int id = stack.back();
+        stack.pop_back();
+        flat_id[id] = (int)order.size();
+        order.push_back(id);
+        const TmpNode &t = b.nodes[id];
+        if (b.nodes[t.right].left >= 0) stack.push_back(t.right);
+        if (b.nodes[t.left].left >= 0) stack.push_back(t.left);
+    }
+    out.nodes.clear();
+    auto ref_of = [&](int id) {
+        const TmpNode &t = b.nodes[id];
+        return t.left >= 0 ? flat_id[id] : leaf_ref(t.first, t.count);
+    };
+    if (order.empty()) {
+        // root is a leaf (or the scene is empty): one node with the leaf and an empty child
+        float4 nd[4];
+        std::memset(nd, 0, sizeof(nd));
+        Box empty;
+        Box root = b.nodes.empty() ? empty : b.nodes[0].box;
+        put_child(nd, 0, root);
+        put_child(nd, 1, empty);
+        int *ref = reinterpret_cast<int *>(&nd[3]);
+        ref[0] = leaf_ref(0, (int)n);
+        ref[1] = leaf_ref(0, 0);
+        out.nodes.assign(nd, nd + 4);
+    } else {
+        out.nodes.resize(order.size() * 4);
+        for (size_t i = 0; i < order.size(); ++i) {
+            const TmpNode &t = b.nodes[order[i]];
+            float4 *nd = &out.nodes[4 * i];
+            std::memset(nd, 0, 4 * sizeof(float4));
+            put_child(nd, 0, b.nodes[t.left].box);
+            put_child(nd, 1, b.nodes[t.right].box);
+            int *ref = reinterpret_cast<int *>(&nd[3]);
+            ref[0] = ref_of(t.left);
+            ref[1] = ref_of(t.right);
+        }
+    }
+    if (b.max_leaf > 127) {
+        err = "BVH: leaf larger than 127 primitives (degenerate input)";
+        return false;
+    }
+    out.prim_order = b.idx;
+    out.depth = b.depth;
+    out.max_leaf = b.max_leaf;
+    return true;
+}
+
+// ============================================================================ lattice
+namespace {
+
+struct D3 {
+    double x, y, z;
+};
+D3 d3(double x, double y, double z) { return {x, y, z}; }
+D3 operator+(D3 a, D3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+D3 operator-(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+D3 operator*(D3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+double dot3(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+D3 cross3(D3 a, D3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+D3 normed(D3 a) { return a * (1.0 / std::sqrt(dot3(a, a))); }
+double arc(D3 a, D3 b) { return std::atan2(std::sqrt(dot3(cross3(a, b), cross3(a, b))), dot3(a, b)); }
+
+// point at fraction f along the great circle a -> b
+D3 arc_point(D3 a, D3 b, double f) {
+    double w = arc(a, b);
+    return normed(a * std::sin((1.0 - f) * w) + b * std::sin(f * w));
+}
+
+}  // namespace
+
+void build_lattice_tables(int n, std::vector<float4> &ico, std::vector<int2> &edges, std::vector<float4> &centre,
+                          std::vector<float4> &layers, int &nl) {
+    // Regular icosahedron: cyclic permutations of (0, +-1, +-phi), in this fixed order.
+    const double g = 0.5 * (1.0 + std::sqrt(5.0));
+    const double raw[12][3] = {{0, 1, g},  {0, -1, g},  {0, 1, -g},  {0, -1, -g}, {1, g, 0},  {-1, g, 0},
+                               {1, -g, 0}, {-1, -g, 0}, {g, 0, 1},  {-g, 0, 1},  {g, 0, -1}, {-g, 0, -1}};
+    D3 V[12];
+    for (int i = 0; i < 12; ++i) V[i] = normed(d3(raw[i][0], raw[i][1], raw[i][2]));
+    // adjacency: unnormalised vertices at distance 2
+    auto adj = [&](int i, int j) {
+        D3 a = d3(raw[i][0], raw[i][1], raw[i][2]), b = d3(raw[j][0], raw[j][1], raw[j][2]);
+        return std::fabs(dot3(a - b, a - b) - 4.0) < 1e-9;
+    };
+    ico.assign(12, make_float4(0, 0, 0, 0));
+    for (int i = 0; i < 12; ++i) ico[i] = make_float4((float)V[i].x, (float)V[i].y, (float)V[i].z, 0.0f);
+    edges.clear();
+    std::vector<int> F;   // 20 oriented faces, lowest vertex first
+    for (int i = 0; i < 12; ++i)
+        for (int j = i + 1; j < 12; ++j) {
+            if (!adj(i, j)) continue;
+            edges.push_back(make_int2(i, j));
+            for (int k = j + 1; k < 12; ++k) {
+                if (!adj(i, k) || !adj(j, k)) continue;
+                D3 c = V[i] + V[j] + V[k];
+                bool ccw = dot3(cross3(V[j] - V[i], V[k] - V[i]), c) > 0.0;
+                F.push_back(i);
+                F.push_back(ccw ? j : k);
+                F.push_back(ccw ? k : j);
+            }
+        }
+    nl = (n + 2) / 3;  // layers a >= 0 with n - 3a >= 1
+    centre.assign(20, make_float4(0, 0, 0, 0));
+    layers.assign((size_t)20 * nl * 3, make_float4(0, 0, 0, 0));
+    for (int f = 0; f < 20; ++f) {
+        D3 W[3] = {V[F[3 * f]], V[F[3 * f + 1]], V[F[3 * f + 2]]};
+        D3 c = normed(W[0] + W[1] + W[2]);
+        centre[f] = make_float4((float)c.x, (float)c.y, (float)c.z, 0.0f);
+        for (int a = 0; a < nl; ++a) {
+            for (int e = 0; e < 3; ++e) {
+                D3 p = W[e], q = W[(e + 1) % 3];
+                layers[((size_t)f * nl + a) * 3 + e] =
+                    make_float4((float)p.x, (float)p.y, (float)p.z, (float)arc(p, q));
+            }
+            if (a + 1 == nl) break;
+            // Eq. 2 (parallelogram rule): the next layer's vertex near W_e is W_e moved by
+            // the vectors to its two layer-a neighbours, projected back onto the sphere.
+            int m = n - 3 * a;
+            D3 nw[3];
+            for (int e = 0; e < 3; ++e) {
+                D3 fwd = arc_point(W[e], W[(e + 1) % 3], 1.0 / m);
+                D3 bwd = arc_point(W[e], W[(e + 2) % 3], 1.0 / m);
+                nw[e] = normed(fwd + bwd - W[e]);
+            }
+            for (int e = 0; e < 3; ++e) W[e] = nw[e];
+        }
+    }
+}
+
+// ============================================================================ sub-rays
+// Sub-cone centres covering a cone of half-angle 1 (fractions of R) and the shrink factor
+// (sub-cone half-angle / R).  K = 6 is the paper's ring of six at R/sqrt(3) (Fig. 5,
+// Eq. 10).  K = 7, 9, 16 add a centre sub-ray and one or two rings; their radii are the
+// smallest that still cover the disc (ring 5 and ring 10 radii for K = 16 were found by a
+// covering search and are checked by sampling in the tests).
+int subray_pattern(int K, double *rho, double *phi, double *shrink) {
+    const double pi = 3.14159265358979323846;
+    int k = 0;
+    switch (K) {
+        case 6:
+            for (int j = 0; j < 6; ++j, ++k) { rho[k] = 0.57735026918962576; phi[k] = j * pi / 3.0; }
+            *shrink = 0.57735026918962576;
+            return 6;
+        case 7:
+            rho[k] = 0.0; phi[k] = 0.0; ++k;
+            for (int j = 0; j < 6; ++j, ++k) { rho[k] = 0.86602540378443865; phi[k] = j * pi / 3.0; }
+            *shrink = 0.5;
+            return 7;
+        case 9:
+            rho[k] = 0.0; phi[k] = 0.0; ++k;
+            for (int j = 0; j < 8; ++j, ++k) { rho[k] = 0.76536686473017954; phi[k] = j * pi / 4.0; }
+            *shrink = 0.41421356237309505;
+            return 9;
+        case 16:
+            rho[k] = 0.0; phi[k] = 0.0; ++k;
+            for (int j = 0; j < 5; ++j, ++k) { rho[k] = 0.45963989297888640; phi[k] = j * 2.0 * pi / 5.0; }
+            for (int j = 0; j < 10; ++j, ++k) { rho[k] = 0.82442949532182900; phi[k] = j * pi / 5.0; }
+            *shrink = 0.33395494494483097;
+            return 16;
+        default:
+            return -1;
+    }
+}
+
+}  // namespace sbr

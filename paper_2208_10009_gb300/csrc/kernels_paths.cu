@@ -1,0 +1,182 @@
+// kernels_paths.cu -- a5 double-count removal (§III.A, first path test): among reception
+// records with the same (Tx, Rx, face sequence) keep the one with the smallest error
+// angle of Eq. 3, ties to the lowest ray id.  Implemented as an open-addressing hash table
+// keyed by a 64-bit hash of the face sequence with a 64-bit atomicMin on
+// (error-angle bits, ray id); a second pass checks every record against its slot's
+// winner so that a hash collision is detected, never silently merged.
+#include "sbr_device.cuh"
+
+namespace sbr {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+__device__ __forceinline__ unsigned long long rec_hash(const RecDev &r) {
+    unsigned long long h = mix64(((unsigned long long)(unsigned)r.tx << 40) ^ ((unsigned long long)(unsigned)r.rx << 8) ^
+                                 (unsigned long long)r.order);
+    for (int j = 0; j < r.order; ++j) h = mix64(h ^ (unsigned long long)(unsigned)(r.faces[j] + 1));
+    return h == ~0ULL ? 0x5bd1e995ULL : h;
+}
+
+__device__ __forceinline__ unsigned long long rec_value(const RecDev &r) {
+    // error angles are >= 0, so their IEEE bits order like the values
+    return ((unsigned long long)__float_as_uint(r.err) << 32) | (unsigned)r.ray;
+}
+
+__device__ __forceinline__ bool same_key(const RecDev &a, const RecDev &b) {
+    if (a.tx != b.tx || a.rx != b.rx || a.order != b.order) return false;
+    for (int j = 0; j < a.order; ++j)
+        if (a.faces[j] != b.faces[j]) return false;
+    return true;
+}
+
+__device__ __forceinline__ long long num_records(const DedupArgs &a) {
+    long long n = a.counters[kRecords];
+    return n < a.rec_cap ? n : a.rec_cap;
+}
+
+__global__ void dedup_insert(DedupArgs a) {
+    const long long n = num_records(a);
+    unsigned long long *keys = a.table, *vals = a.table + a.slots;
+    const unsigned long long mask = (unsigned long long)a.slots - 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        RecDev r = a.recs[i];
+        unsigned long long h = rec_hash(r), v = rec_value(r);
+        unsigned long long s = h & mask;
+        for (long long probe = 0; probe < a.slots; ++probe) {
+            unsigned long long prev = atomicCAS(keys + s, ~0ULL, h);
+            if (prev == ~0ULL || prev == h) {
+                atomicMin(vals + s, v);
+                a.recs[i].slot = (int)s;
+                break;
+            }
+            s = (s + 1) & mask;
+        }
+    }
+}
+
+__global__ void dedup_select(DedupArgs a) {
+    const long long n = num_records(a);
+    const unsigned long long *vals = a.table + a.slots;
+    int *winner = reinterpret_cast<int *>(a.table + 2 * a.slots);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        RecDev r = a.recs[i];
+        if (r.slot < 0) continue;
+        if (vals[r.slot] != rec_value(r)) continue;
+        winner[r.slot] = (int)i;
+        unsigned long long p = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kPaths), 1ULL);
+        if ((long long)p >= a.path_cap) continue;
+        sbr_path_record out;
+        out.tx = r.tx;
+        out.rx = r.rx;
+        out.ray = r.ray;
+        out.order = r.order;
+        for (int j = 0; j < kMaxOrder; ++j) out.faces[j] = r.faces[j];
+        out.rough_err = r.err;
+        out.rough_dray = r.dray;
+        out.iters = 0;
+        out.valid = 0;
+        float4 d = __ldg(a.dirs + r.ray);
+        out.dir[0] = d.x;
+        out.dir[1] = d.y;
+        out.dir[2] = d.z;
+        out.err = r.err;
+        out.delay = 0.0;
+        out.aod[0] = out.aod[1] = out.aoa[0] = out.aoa[1] = 0.0f;
+        out.power_dbm = 0.0f;
+        out.flags = 0;
+        a.paths[p] = out;
+    }
+}
+
+__global__ void dedup_verify(DedupArgs a) {
+    const long long n = num_records(a);
+    const int *winner = reinterpret_cast<const int *>(a.table + 2 * a.slots);
+    unsigned bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const RecDev &r = a.recs[i];
+        if (r.slot < 0) {
+            ++bad;
+            continue;
+        }
+        int w = winner[r.slot];
+        if (w < 0 || !same_key(r, a.recs[w])) ++bad;
+    }
+    if (bad) atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kCollisions), (unsigned long long)bad);
+}
+
+cudaError_t launch_dedup(const DedupArgs &a, int num_sms, cudaStream_t s) {
+    // keys and values start at all-ones (empty / +inf); winners at -1
+    cudaError_t e = cudaMemsetAsync(a.table, 0xFF, (size_t)a.slots * (2 * sizeof(unsigned long long) + sizeof(int)), s);
+    if (e != cudaSuccess) return e;
+    int grid = num_sms * 4;
+    dedup_insert<<<grid, 256, 0, s>>>(a);
+    dedup_select<<<grid, 256, 0, s>>>(a);
+    dedup_verify<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------- pairs
+// Group path indices by (tx, rx) pair: counts, exclusive scan (one block), scatter.
+__global__ void pair_count(PairArgs a) {
+    long long n = a.counters[kPaths];
+    if (n > a.path_cap) n = a.path_cap;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int p = a.paths[i].tx * a.nrx + a.paths[i].rx;
+        atomicAdd(a.pair_count + p, 1);
+    }
+}
+
+__global__ void pair_scan(PairArgs a) {
+    // single block: exclusive scan of pair_count[0..npairs) into pair_count, total at [npairs]
+    __shared__ int carry;
+    __shared__ int buf[1024];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < a.npairs; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < a.npairs ? a.pair_count[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            int t = threadIdx.x >= off ? buf[threadIdx.x - off] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < a.npairs) a.pair_count[i] = carry + buf[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += buf[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a.pair_count[a.npairs] = carry;
+}
+
+__global__ void pair_scatter(PairArgs a, int *cursor) {
+    long long n = a.counters[kPaths];
+    if (n > a.path_cap) n = a.path_cap;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int p = a.paths[i].tx * a.nrx + a.paths[i].rx;
+        int at = atomicAdd(cursor + p, 1);
+        a.pair_idx[at] = (int)i;
+    }
+}
+
+cudaError_t launch_pair_bucket(const PairArgs &a, cudaStream_t s) {
+    // cursor lives after pair_idx: [npairs] ints (caller sized pair_idx + npairs)
+    int *cursor = a.pair_idx + a.path_cap;
+    cudaError_t e = cudaMemsetAsync(a.pair_count, 0, sizeof(int) * (size_t)(a.npairs + 1), s);
+    if (e != cudaSuccess) return e;
+    pair_count<<<256, 256, 0, s>>>(a);
+    pair_scan<<<1, 1024, 0, s>>>(a);
+    e = cudaMemcpyAsync(cursor, a.pair_count, sizeof(int) * (size_t)a.npairs, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    pair_scatter<<<256, 256, 0, s>>>(a, cursor);
+    return cudaGetLastError();
+}
+
+}  // namespace sbr

@@ -1,0 +1,260 @@
+// kernels_trace.cu -- a1 equiangular ray generation (§II.B, Eq. 1-2) and a2-a4 the
+// persistent trace kernel: BVH closest hit with a watertight triangle test, specular
+// reflection up to max_order (Fig. 4) and the reception judgment with the error angle
+// of Eq. 3 on every segment.
+#include "sbr_device.cuh"
+
+namespace sbr {
+
+// ----------------------------------------------------------------------------- a1
+// Point j of m equal-angle steps along the great circle u -> v (angle om): Eq. 1 asks the
+// points of a layer edge to subtend equal angles.  Normalised afterwards.
+__device__ __forceinline__ float3 arc_point(float3 u, float3 v, float om, int j, int m) {
+    float a = sinf(om * (float)(m - j) / (float)m);
+    float b = sinf(om * (float)j / (float)m);
+    float3 p = u * a + v * b;
+    float inv = 1.0f / sqrtf(dot(p, p));
+    return p * inv;
+}
+
+// interior points of layers 1..a of a face: S(a) = sum_{a'=1..a} 3(n - 3a')
+__device__ __forceinline__ long long layer_prefix(int n, long long a) { return (6LL * n * a - 9LL * a * a - 9LL * a) / 2; }
+
+__global__ void raygen_kernel(LatticeDev L, float4 *__restrict__ dirs, long long N) {
+    const int n = L.n;
+    const long long n_edge = 30LL * (n - 1);
+    const long long per_face = (long long)(n - 1) * (n - 2) / 2;
+    const long long layer_pts = layer_prefix(n, L.nl - 1);   // points on layers 1..nl-1
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N;
+         id += (long long)gridDim.x * blockDim.x) {
+        float3 d;
+        if (id < 12) {
+            d = f3(__ldg(L.ico + id));
+        } else if (id < 12 + n_edge) {
+            long long r = id - 12;
+            int e = (int)(r / (n - 1)), j = (int)(r % (n - 1)) + 1;
+            int2 ed = __ldg(L.edges + e);
+            d = arc_point(f3(__ldg(L.ico + ed.x)), f3(__ldg(L.ico + ed.y)), L.edge_angle, j, n);
+        } else {
+            long long r = id - 12 - n_edge;
+            int f = (int)(r / per_face);
+            long long q = r % per_face;
+            if (q >= layer_pts) {
+                d = f3(__ldg(L.centre + f));   // n = 0 mod 3: the face centre ray
+            } else {
+                // layer a >= 1 with S(a-1) <= q < S(a): estimate from the quadratic, then fix
+                float B = 3.0f * n - 4.5f;
+                float disc = fmaxf(B * B - 18.0f * (float)q, 0.0f);
+                long long a = (long long)((B - sqrtf(disc)) / 9.0f) + 1;
+                if (a < 1) a = 1;
+                if (a > L.nl - 1) a = L.nl - 1;
+                while (a > 1 && layer_prefix(n, a - 1) > q) --a;
+                while (layer_prefix(n, a) <= q) ++a;
+                long long b = q - layer_prefix(n, a - 1);
+                int m = n - 3 * (int)a;
+                int e = (int)(b / m), j = (int)(b % m);
+                const float4 *W = L.layers + ((size_t)f * L.nl + a) * 3;
+                float4 w0 = __ldg(W + e), w1 = __ldg(W + (e == 2 ? 0 : e + 1));
+                d = arc_point(f3(w0), f3(w1), w0.w, j, m);
+            }
+        }
+        dirs[id] = make_float4(d.x, d.y, d.z, 0.0f);
+    }
+}
+
+cudaError_t launch_raygen(const LatticeDev &lat, float4 *dirs, int64_t N, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (N + 255) / 256;
+    int grid = (int)(want < (long long)sms * 16 ? want : (long long)sms * 16);
+    if (grid < 1) grid = 1;
+    raygen_kernel<<<grid, 256, 0, s>>>(lat, dirs, (long long)N);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------- a2-a4
+__device__ __forceinline__ int slab2_expand(const float4 *node, const RayPre &r, float tmax, float rad, float &e0,
+                                            float &e1) {
+    float4 a = __ldg(node + 0), b = __ldg(node + 1), c = __ldg(node + 2);
+    float lx0 = (a.x - rad - r.o.x) * r.inv.x, hx0 = (a.w + rad - r.o.x) * r.inv.x;
+    float ly0 = (a.y - rad - r.o.y) * r.inv.y, hy0 = (b.x + rad - r.o.y) * r.inv.y;
+    float lz0 = (a.z - rad - r.o.z) * r.inv.z, hz0 = (b.y + rad - r.o.z) * r.inv.z;
+    float lx1 = (b.z - rad - r.o.x) * r.inv.x, hx1 = (c.y + rad - r.o.x) * r.inv.x;
+    float ly1 = (b.w - rad - r.o.y) * r.inv.y, hy1 = (c.z + rad - r.o.y) * r.inv.y;
+    float lz1 = (c.x - rad - r.o.z) * r.inv.z, hz1 = (c.w + rad - r.o.z) * r.inv.z;
+    float n0 = fmaxf(fmaxf(fminf(lx0, hx0), fminf(ly0, hy0)), fmaxf(fminf(lz0, hz0), 0.0f));
+    float f0 = fminf(fminf(fmaxf(lx0, hx0), fmaxf(ly0, hy0)), fminf(fmaxf(lz0, hz0), tmax)) * 1.0000005f;
+    float n1 = fmaxf(fmaxf(fminf(lx1, hx1), fminf(ly1, hy1)), fmaxf(fminf(lz1, hz1), 0.0f));
+    float f1 = fminf(fminf(fmaxf(lx1, hx1), fmaxf(ly1, hy1)), fminf(fmaxf(lz1, hz1), tmax)) * 1.0000005f;
+    e0 = n0;
+    e1 = n1;
+    return (n0 <= f0 ? 1 : 0) | (n1 <= f1 ? 2 : 0);
+}
+
+struct LaneRay {
+    float3 o, d;
+    float L;
+    int k, prev, txi, ray;
+};
+
+// Reception judgment on segment o + s d, s in [0, tseg], of a ray that has travelled L
+// metres before it: every Rx whose foot lies on the segment and whose error angle
+// (Eq. 3) is within the cone emits a record.
+__device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, const LaneRay &st, float tseg,
+                                          const int *faces_sh, int stride_sh, unsigned &rx_tests) {
+    const RxDev &R = a.rx;
+    if (R.nrx == 0) return;
+    float tcap = fminf(tseg, max_foot(R, st.o, st.d));
+    if (!(tcap >= 0.0f)) return;
+    float rad = (st.L + tcap) * a.tan_cone * 1.001f + 1e-5f;
+    int stack[kStackDepth];
+    int sp = 0;
+    int node = 0;
+    for (;;) {
+        if (!is_leaf(node)) {
+            const float4 *nd = R.nodes + 4 * (size_t)node;
+            float e0, e1;
+            int m = slab2_expand(nd, r, tcap, rad, e0, e1);
+            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 3));
+            if (m == 3) {
+                stack[sp++] = refs.y;
+                node = refs.x;
+                continue;
+            } else if (m == 1) {
+                node = refs.x;
+                continue;
+            } else if (m == 2) {
+                node = refs.y;
+                continue;
+            }
+        } else {
+            int first = leaf_first(node), cnt = leaf_count(node);
+            for (int i = first; i < first + cnt; ++i) {
+                float4 p = __ldg(R.pts + i);
+                ++rx_tests;
+                float3 w = f3(p) - st.o;
+                float s = dot(w, st.d);
+                if (s < 0.0f || s > tseg) continue;
+                float3 q = w - st.d * s;
+                float dperp = sqrtf(dot(q, q));
+                float dray = st.L + s;
+                float err = atan2f(dperp, dray);
+                if (!(err <= a.cone)) continue;
+                unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kRecords), 1ULL);
+                if ((long long)slot < a.rec_cap) {
+                    RecDev rec;
+                    rec.tx = st.txi;
+                    rec.rx = __float_as_int(p.w);
+                    rec.ray = st.ray;
+                    rec.order = st.k;
+#pragma unroll
+                    for (int j = 0; j < kMaxOrder; ++j) rec.faces[j] = j < st.k ? faces_sh[j * stride_sh] : -1;
+                    rec.err = err;
+                    rec.dray = dray;
+                    rec.slot = -1;
+                    rec.pad = 0;
+                    int4 *dst = reinterpret_cast<int4 *>(a.recs + slot);
+                    const int4 *src = reinterpret_cast<const int4 *>(&rec);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) dst[j] = src[j];
+                }
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+}
+
+// Persistent trace kernel.  Each warp keeps 32 rays in registers; after every segment the
+// lanes whose ray ended (miss or order cap) take fresh ray ids from a global counter with
+// one warp-aggregated atomic (ballot + popc), so warps stay full until the pool drains.
+__global__ void __launch_bounds__(128) trace_kernel(TraceArgs a) {
+    extern __shared__ int faces_sh_all[];                // [kMaxOrder][blockDim.x]
+    int *faces_sh = faces_sh_all + threadIdx.x;
+    const int stride_sh = blockDim.x;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long total = (long long)a.ntx * a.nrays_per_tx;
+    unsigned seg = 0, nodes = 0, tris = 0, rxt = 0;
+    bool alive = false, pool_empty = false;
+    LaneRay st;
+    st.o = st.d = make_float3(0, 0, 0);
+    st.L = 0.0f;
+    st.k = st.prev = st.txi = st.ray = 0;
+    for (;;) {
+        unsigned need = __ballot_sync(0xffffffffu, !alive);
+        if (need && !pool_empty) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kRayHead),
+                                            (unsigned long long)__popc(need));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if ((long long)base >= total) pool_empty = true;
+            if (!alive) {
+                long long gid = (long long)base + __popc(need & lt_mask);
+                if (gid < total) {
+                    st.txi = (int)(gid / a.nrays_per_tx);
+                    st.ray = (int)(gid - (long long)st.txi * a.nrays_per_tx);
+                    st.o = f3(__ldg(a.tx + st.txi));
+                    st.d = f3(__ldg(a.dirs + st.ray));
+                    st.L = 0.0f;
+                    st.k = 0;
+                    st.prev = -1;
+                    alive = true;
+                    if (a.dump_stride > 0 && st.ray % a.dump_stride == 0) {
+                        int *df = a.dump_faces + ((size_t)st.txi * a.dump_per_tx + st.ray / a.dump_stride) *
+                                                     (a.max_order + 1);
+                        for (int j = 0; j <= a.max_order; ++j) df[j] = -2;
+                    }
+                }
+            }
+        }
+        if (__ballot_sync(0xffffffffu, alive) == 0) break;
+        if (!alive) continue;
+        RayPre r = make_ray(st.o, st.d);
+        float th;
+        int face;
+        int hit = closest_hit(a.scene, r, a.scene.tmin, INFINITY, st.prev, th, face, nodes, tris);
+        ++seg;
+        if (a.dump_stride > 0 && st.ray % a.dump_stride == 0)
+            a.dump_faces[((size_t)st.txi * a.dump_per_tx + st.ray / a.dump_stride) * (a.max_order + 1) + st.k] =
+                hit >= 0 ? face : -1;
+        float tseg = hit >= 0 ? th : INFINITY;
+        reception(a, r, st, tseg, faces_sh, stride_sh, rxt);
+        if (hit < 0 || st.k == a.max_order) {
+            alive = false;
+            continue;
+        }
+        // specular reflection on the hit face's plane
+        float4 pl = __ldg(a.scene.planes + face);
+        float3 nrm = f3(pl);
+        st.o = st.o + st.d * th;
+        st.d = st.d - nrm * (2.0f * dot(st.d, nrm));
+        st.L += th;
+        faces_sh[st.k * stride_sh] = face;
+        st.prev = face;
+        ++st.k;
+    }
+    // one atomic per warp per counter
+    unsigned s0 = __reduce_add_sync(0xffffffffu, seg), s1 = __reduce_add_sync(0xffffffffu, nodes);
+    unsigned s2 = __reduce_add_sync(0xffffffffu, tris), s3 = __reduce_add_sync(0xffffffffu, rxt);
+    if (lane == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kSegments), (unsigned long long)s0);
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kNodeVisits), (unsigned long long)s1);
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kTriTests), (unsigned long long)s2);
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kRxTests), (unsigned long long)s3);
+    }
+}
+
+int trace_blocks_per_sm(int block) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel, block, (size_t)kMaxOrder * block * sizeof(int));
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_trace(const TraceArgs &a, int grid, int block, cudaStream_t s) {
+    trace_kernel<<<grid, block, (size_t)kMaxOrder * block * sizeof(int), s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sbr

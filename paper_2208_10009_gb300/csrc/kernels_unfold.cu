@@ -1,0 +1,181 @@
+// kernels_unfold.cu -- a10 the fixed-face-sequence unfolding and its adjoint.
+//
+// Mirroring through face plane (n, h) is M(x) = H x + 2 h n with H = I - 2 n n^T.  For
+// faces f_1..f_k: Rx' = M_1(...M_k(Rx)) = A Rx + a0 with A = H_1 ... H_k; the last Tx image
+// Tx^(k) = M_k(...M_1(Tx)) = A^T Tx + b0.  With w = Rx' - Tx and d(az, el) the launch
+// direction:
+//   miss  = A^T (w - (w.d) d)     real-space vector from the foot of Rx on the last leg to Rx
+//   delay = |w| / c0
+//   AOD   = (atan2(w_y, w_x), atan2(w_z, hypot(w_x, w_y)))
+//   AOA   = same angles of v = Tx^(k) - Rx
+// Applying A to a vector is mirroring (linear part) through f_k first, then f_{k-1}, ..., f_1;
+// A^T mirrors through f_1 first.  The adjoint recomputes w, v and d instead of storing them.
+#include "sbr_device.cuh"
+
+namespace sbr {
+
+struct UnfoldPath {
+    float3 tx, rx;
+    float az, el;
+    int k;
+    int faces[kMaxOrder];
+};
+
+__device__ __forceinline__ void load_unfold(const UnfoldArgs &a, long long i, UnfoldPath &u) {
+    u.tx = make_float3(a.tx[3 * i], a.tx[3 * i + 1], a.tx[3 * i + 2]);
+    u.rx = make_float3(a.rx[3 * i], a.rx[3 * i + 1], a.rx[3 * i + 2]);
+    u.az = a.az_el[2 * i];
+    u.el = a.az_el[2 * i + 1];
+    int k = a.order[i];
+    u.k = k < 0 ? 0 : (k > kMaxOrder ? kMaxOrder : k);
+    const int4 *f4 = reinterpret_cast<const int4 *>(a.faces + 8 * i);
+    int4 lo = f4[0], hi = f4[1];
+    u.faces[0] = lo.x; u.faces[1] = lo.y; u.faces[2] = lo.z; u.faces[3] = lo.w;
+    u.faces[4] = hi.x; u.faces[5] = hi.y; u.faces[6] = hi.z; u.faces[7] = hi.w;
+}
+
+// face ids come from the caller: a path with an id outside [0, nf) yields NaN outputs
+__device__ __forceinline__ bool unfold_ids_ok(const UnfoldArgs &a, const UnfoldPath &u) {
+    for (int j = 0; j < u.k; ++j)
+        if (u.faces[j] < 0 || u.faces[j] >= a.nf) return false;
+    return true;
+}
+
+// x -> A x (reverse order), affine when `point`
+__device__ __forceinline__ float3 apply_A(const SceneDev &S, const UnfoldPath &u, float3 x, bool point) {
+#pragma unroll
+    for (int j = kMaxOrder - 1; j >= 0; --j) {
+        if (j >= u.k) continue;
+        float4 pl = __ldg(S.planes + u.faces[j]);
+        float3 n = f3(pl);
+        float s = dot(n, x) - (point ? pl.w : 0.0f);
+        x = x - n * (2.0f * s);
+    }
+    return x;
+}
+
+// x -> A^T x (forward order), affine when `point`
+__device__ __forceinline__ float3 apply_AT(const SceneDev &S, const UnfoldPath &u, float3 x, bool point) {
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j) {
+        if (j >= u.k) break;
+        float4 pl = __ldg(S.planes + u.faces[j]);
+        float3 n = f3(pl);
+        float s = dot(n, x) - (point ? pl.w : 0.0f);
+        x = x - n * (2.0f * s);
+    }
+    return x;
+}
+
+__device__ __forceinline__ void angles(float3 w, float &az, float &el) {
+    az = atan2f(w.y, w.x);
+    el = atan2f(w.z, sqrtf(w.x * w.x + w.y * w.y));
+}
+
+// gradient of (az, el) of w with respect to w
+__device__ __forceinline__ void angles_grad(float3 w, float3 &gaz, float3 &gel) {
+    float rho2 = w.x * w.x + w.y * w.y, rho = sqrtf(rho2), r2 = rho2 + w.z * w.z;
+    gaz = make_float3(-w.y / rho2, w.x / rho2, 0.0f);
+    float c = 1.0f / (r2 * rho);
+    gel = make_float3(-w.x * w.z * c, -w.y * w.z * c, rho / r2);
+}
+
+__global__ void unfold_fwd_kernel(UnfoldArgs a) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x) {
+        UnfoldPath u;
+        load_unfold(a, i, u);
+        if (!unfold_ids_ok(a, u)) {
+            for (int j = 0; j < 8; ++j) a.out[8 * i + j] = __int_as_float(0x7fc00000);
+            continue;
+        }
+        float3 rxp = apply_A(a.scene, u, u.rx, true);
+        float3 w = rxp - u.tx;
+        float se, ce, sa, ca;
+        sincosf(u.el, &se, &ce);
+        sincosf(u.az, &sa, &ca);
+        float3 d = make_float3(ce * ca, ce * sa, se);
+        float3 m = w - d * dot(w, d);
+        float3 miss = apply_AT(a.scene, u, m, false);
+        float3 txk = apply_AT(a.scene, u, u.tx, true);
+        float3 v = txk - u.rx;
+        float *o = a.out + 8 * i;
+        o[0] = miss.x;
+        o[1] = miss.y;
+        o[2] = miss.z;
+        o[3] = sqrtf(dot(w, w)) * (float)(1.0 / kC0);
+        angles(w, o[4], o[5]);
+        angles(v, o[6], o[7]);
+    }
+}
+
+__global__ void unfold_bwd_kernel(UnfoldArgs a) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < a.n; i += (long long)gridDim.x * blockDim.x) {
+        UnfoldPath u;
+        load_unfold(a, i, u);
+        if (!unfold_ids_ok(a, u)) {
+            const float nan = __int_as_float(0x7fc00000);
+            for (int j = 0; j < 3; ++j) a.grad_tx[3 * i + j] = a.grad_rx[3 * i + j] = nan;
+            a.grad_az_el[2 * i] = a.grad_az_el[2 * i + 1] = nan;
+            continue;
+        }
+        const float *g = a.grad_out + 8 * i;
+        // recompute the forward quantities
+        float3 rxp = apply_A(a.scene, u, u.rx, true);
+        float3 w = rxp - u.tx;
+        float se, ce, sa, ca;
+        sincosf(u.el, &se, &ce);
+        sincosf(u.az, &sa, &ca);
+        float3 d = make_float3(ce * ca, ce * sa, se);
+        float3 d_az = make_float3(-ce * sa, ce * ca, 0.0f);
+        float3 d_el = make_float3(-se * ca, -se * sa, ce);
+        float3 txk = apply_AT(a.scene, u, u.tx, true);
+        float3 v = txk - u.rx;
+        float wd = dot(w, d);
+        // miss = A^T (w - (w.d) d): pull g_miss back into unfolded space
+        float3 gm = apply_A(a.scene, u, make_float3(g[0], g[1], g[2]), false);
+        float gmd = dot(gm, d);
+        float3 gw = gm - d * gmd;
+        float3 gd = (gm * wd + w * gmd) * -1.0f;
+        // delay
+        float wn = sqrtf(dot(w, w));
+        gw = gw + w * (g[3] * (float)(1.0 / kC0) / wn);
+        // AOD angles of w
+        float3 gaz, gel;
+        angles_grad(w, gaz, gel);
+        gw = gw + gaz * g[4] + gel * g[5];
+        // AOA angles of v = A^T Tx + b0 - Rx
+        angles_grad(v, gaz, gel);
+        float3 gv = gaz * g[6] + gel * g[7];
+        float3 gtx = gw * -1.0f + apply_A(a.scene, u, gv, false);
+        float3 grx = apply_AT(a.scene, u, gw, false) - gv;
+        a.grad_tx[3 * i] = gtx.x;
+        a.grad_tx[3 * i + 1] = gtx.y;
+        a.grad_tx[3 * i + 2] = gtx.z;
+        a.grad_rx[3 * i] = grx.x;
+        a.grad_rx[3 * i + 1] = grx.y;
+        a.grad_rx[3 * i + 2] = grx.z;
+        a.grad_az_el[2 * i] = dot(gd, d_az);
+        a.grad_az_el[2 * i + 1] = dot(gd, d_el);
+    }
+}
+
+static int unfold_grid(long long n) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (n + 255) / 256;
+    long long cap = (long long)sms * 8;
+    return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+cudaError_t launch_unfold_fwd(const UnfoldArgs &a, cudaStream_t s) {
+    unfold_fwd_kernel<<<unfold_grid(a.n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unfold_bwd(const UnfoldArgs &a, cudaStream_t s) {
+    unfold_bwd_kernel<<<unfold_grid(a.n), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sbr

@@ -1,0 +1,215 @@
+// sbr_device.cuh -- device-side geometry: vector helpers, ray/box slab test, watertight
+// ray/triangle test, BVH closest-hit and any-hit traversal, receiver candidate query.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "sbr_internal.h"
+
+namespace sbr {
+
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float comp(float3 v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : v.z); }
+
+struct dvec3 {
+    double x, y, z;
+};
+__device__ __forceinline__ dvec3 dv(double x, double y, double z) { return {x, y, z}; }
+__device__ __forceinline__ dvec3 operator+(dvec3 a, dvec3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ dvec3 operator-(dvec3 a, dvec3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ dvec3 operator*(dvec3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ double ddot(dvec3 a, dvec3 b) { return fma(a.x, b.x, fma(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ dvec3 dcross(dvec3 a, dvec3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double dnorm(dvec3 a) { return sqrt(ddot(a, a)); }
+
+// Per-ray precomputation for the slab test and the watertight triangle test.
+struct RayPre {
+    float3 o, d, inv;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ RayPre make_ray(float3 o, float3 d) {
+    RayPre r;
+    r.o = o;
+    r.d = d;
+    // 1/0 -> +-inf keeps the slab test correct for axis-parallel rays
+    r.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (comp(d, kz) < 0.0f) {
+        int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    r.kx = kx;
+    r.ky = ky;
+    r.kz = kz;
+    float dz = comp(d, kz);
+    r.Sx = comp(d, kx) / dz;
+    r.Sy = comp(d, ky) / dz;
+    r.Sz = 1.0f / dz;
+    return r;
+}
+
+// Slab test of both children of a BVH node; returns a 2-bit hit mask and entry distances.
+// The far bound is widened by a few ulps so that rounding never culls a box the ray
+// actually touches (zero-thickness boxes of axis-aligned walls included).
+__device__ __forceinline__ int slab2(const float4 *node, const RayPre &r, float tmin, float tmax, float &t0,
+                                     float &t1) {
+    float4 a = __ldg(node + 0), b = __ldg(node + 1), c = __ldg(node + 2);
+    float lx0 = (a.x - r.o.x) * r.inv.x, hx0 = (a.w - r.o.x) * r.inv.x;
+    float ly0 = (a.y - r.o.y) * r.inv.y, hy0 = (b.x - r.o.y) * r.inv.y;
+    float lz0 = (a.z - r.o.z) * r.inv.z, hz0 = (b.y - r.o.z) * r.inv.z;
+    float lx1 = (b.z - r.o.x) * r.inv.x, hx1 = (c.y - r.o.x) * r.inv.x;
+    float ly1 = (b.w - r.o.y) * r.inv.y, hy1 = (c.z - r.o.y) * r.inv.y;
+    float lz1 = (c.x - r.o.z) * r.inv.z, hz1 = (c.w - r.o.z) * r.inv.z;
+    float n0 = fmaxf(fmaxf(fminf(lx0, hx0), fminf(ly0, hy0)), fmaxf(fminf(lz0, hz0), tmin));
+    float f0 = fminf(fminf(fmaxf(lx0, hx0), fmaxf(ly0, hy0)), fminf(fmaxf(lz0, hz0), tmax)) * 1.0000005f;
+    float n1 = fmaxf(fmaxf(fminf(lx1, hx1), fminf(ly1, hy1)), fmaxf(fminf(lz1, hz1), tmin));
+    float f1 = fminf(fminf(fmaxf(lx1, hx1), fmaxf(ly1, hy1)), fminf(fmaxf(lz1, hz1), tmax)) * 1.0000005f;
+    t0 = n0;
+    t1 = n1;
+    return (n0 <= f0 ? 1 : 0) | (n1 <= f1 ? 2 : 0);
+}
+
+// Watertight ray/triangle intersection (Woop, Benthin, Wald, JCGT 2013): edge functions in a
+// sheared, permuted frame; an exactly-zero edge function is re-evaluated in double so
+// that rays through a shared edge or vertex hit at least one of the triangles.
+// Returns t, or a negative value on a miss.
+__device__ __forceinline__ float tri_watertight(const RayPre &r, float4 A4, float4 B4, float4 C4) {
+    float3 A = f3(A4) - r.o, B = f3(B4) - r.o, C = f3(C4) - r.o;
+    float Az = comp(A, r.kz), Bz = comp(B, r.kz), Cz = comp(C, r.kz);
+    float Ax = comp(A, r.kx) - r.Sx * Az, Ay = comp(A, r.ky) - r.Sy * Az;
+    float Bx = comp(B, r.kx) - r.Sx * Bz, By = comp(B, r.ky) - r.Sy * Bz;
+    float Cx = comp(C, r.kx) - r.Sx * Cz, Cy = comp(C, r.ky) - r.Sy * Cz;
+    float U = Cx * By - Cy * Bx;
+    float V = Ax * Cy - Ay * Cx;
+    float W = Bx * Ay - By * Ax;
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+        V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+        W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
+    float det = U + V + W;
+    if (det == 0.0f) return -1.0f;
+    float T = U * (r.Sz * Az) + V * (r.Sz * Bz) + W * (r.Sz * Cz);
+    return T / det;
+}
+
+// Closest hit along o + t d over t in (tmin, tmax], skipping triangles of face `skip`.
+// Ties in t go to the lower face id, then the lower triangle index.  Returns the
+// triangle index (BVH order) or -1; t_out, face_out set on a hit.
+__device__ __forceinline__ int closest_hit(const SceneDev &S, const RayPre &r, float tmin, float tmax, int skip,
+                                           float &t_out, int &face_out, unsigned &nodes_visited,
+                                           unsigned &tris_tested) {
+    int stack[kStackDepth];
+    int sp = 0;
+    int node = 0;
+    float tbest = tmax;
+    int best = -1, bface = 0x7fffffff;
+    for (;;) {
+        if (!is_leaf(node)) {
+            ++nodes_visited;
+            const float4 *nd = S.nodes + 4 * (size_t)node;
+            float e0, e1;
+            int m = slab2(nd, r, tmin, tbest, e0, e1);
+            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 3));
+            if (m == 3) {
+                int nearc = e0 <= e1 ? refs.x : refs.y;
+                int farc = e0 <= e1 ? refs.y : refs.x;
+                stack[sp++] = farc;
+                node = nearc;
+                continue;
+            } else if (m == 1) {
+                node = refs.x;
+                continue;
+            } else if (m == 2) {
+                node = refs.y;
+                continue;
+            }
+        } else {
+            int first = leaf_first(node), cnt = leaf_count(node);
+            for (int i = first; i < first + cnt; ++i) {
+                const float4 *t = S.tris + 3 * (size_t)i;
+                float4 a = __ldg(t), b = __ldg(t + 1), c = __ldg(t + 2);
+                int f = __float_as_int(a.w);
+                if (f == skip) continue;
+                ++tris_tested;
+                float th = tri_watertight(r, a, b, c);
+                if (!(th > tmin) || th > tbest) continue;
+                if (th < tbest || f < bface || (f == bface && i < best)) {
+                    tbest = th;
+                    best = i;
+                    bface = f;
+                }
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    t_out = tbest;
+    face_out = bface;
+    return best;
+}
+
+// Any hit of the segment o + t d, t in (tmin, tmax), ignoring faces fa and fb.
+__device__ __forceinline__ bool any_hit(const SceneDev &S, const RayPre &r, float tmin, float tmax, int fa, int fb) {
+    int stack[kStackDepth];
+    int sp = 0;
+    int node = 0;
+    for (;;) {
+        if (!is_leaf(node)) {
+            const float4 *nd = S.nodes + 4 * (size_t)node;
+            float e0, e1;
+            int m = slab2(nd, r, tmin, tmax, e0, e1);
+            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 3));
+            if (m == 3) {
+                stack[sp++] = refs.y;
+                node = refs.x;
+                continue;
+            } else if (m == 1) {
+                node = refs.x;
+                continue;
+            } else if (m == 2) {
+                node = refs.y;
+                continue;
+            }
+        } else {
+            int first = leaf_first(node), cnt = leaf_count(node);
+            for (int i = first; i < first + cnt; ++i) {
+                const float4 *t = S.tris + 3 * (size_t)i;
+                float4 a = __ldg(t), b = __ldg(t + 1), c = __ldg(t + 2);
+                int f = __float_as_int(a.w);
+                if (f == fa || f == fb) continue;
+                float th = tri_watertight(r, a, b, c);
+                if (th > tmin && th < tmax) return true;
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    return false;
+}
+
+// Largest foot parameter s = (p - o).d of any point p of box [lo, hi].
+__device__ __forceinline__ float max_foot(const RxDev &R, float3 o, float3 d) {
+    float s = (d.x > 0 ? R.hi[0] : R.lo[0]) * d.x + (d.y > 0 ? R.hi[1] : R.lo[1]) * d.y +
+              (d.z > 0 ? R.hi[2] : R.lo[2]) * d.z;
+    return s - dot(o, d);
+}
+
+}  // namespace sbr

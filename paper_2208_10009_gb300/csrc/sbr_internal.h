@@ -1,0 +1,254 @@
+// sbr_internal.h -- device layouts and launch wrappers shared by the library's
+// translation units.  Not part of the public ABI (include/sbr.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sbr.h"
+
+namespace sbr {
+
+constexpr int kMaxOrder = SBR_MAX_ORDER;
+constexpr double kC0 = 299792458.0;
+constexpr int kLeafMax = 4;        // triangles per BVH leaf (target)
+constexpr int kStackDepth = 64;    // traversal stack entries (BVH depth is capped below this)
+
+// Device counters of one launch (int64 each).
+enum Counter {
+    kRays = 0, kSegments, kNodeVisits, kTriTests, kRxTests, kRecords, kPaths, kCollisions,
+    kRayHead, kBatchHead, kBatchDone, kErrorFlags, kNumCounters = 16
+};
+
+// BVH node: both children's boxes in one 64-byte node (4 x float4).
+//   f[0] = (c0.lo.x, c0.lo.y, c0.lo.z, c0.hi.x)
+//   f[1] = (c0.hi.y, c0.hi.z, c1.lo.x, c1.lo.y)
+//   f[2] = (c1.lo.z, c1.hi.x, c1.hi.y, c1.hi.z)
+//   f[3] = (child0 ref, child1 ref, -, -) as int bits
+// A child ref >= 0 is an inner node index; a leaf ref has bit 31 set, 7 bits of
+// primitive count (bits 24-30) and a 24-bit first-primitive index.
+__host__ __device__ inline int leaf_ref(int first, int count) {
+    return (int)(0x80000000u | ((unsigned)count << 24) | (unsigned)first);
+}
+__host__ __device__ inline bool is_leaf(int ref) { return ref < 0; }
+__host__ __device__ inline int leaf_first(int ref) { return ref & 0xFFFFFF; }
+__host__ __device__ inline int leaf_count(int ref) { return (ref >> 24) & 0x7F; }
+
+// face plane in double: n.x = h
+struct __align__(32) Plane64 {
+    double x, y, z, w;
+};
+
+struct SceneDev {
+    const float4 *nodes;      // 4 per node
+    const float4 *tris;       // 3 per triangle: (v0, face id bits), (v1, 0), (v2, 0)
+    const float4 *planes;     // per face: (n, h) with n.x = h on the plane
+    const Plane64 *planes_d;  // same in double
+    const float *face_eps;    // per face relative permittivity (<= 0: perfect reflector)
+    const int *face_tri_off;  // CSR over faces -> triangle indices (BVH order)
+    const int *face_tri_idx;
+    int nt, nf, nnodes;
+    float tmin;               // hits need t > tmin (1e-7 x scene diagonal)
+};
+
+struct RxDev {
+    const float4 *nodes;      // BVH over receivers (same node layout)
+    const float4 *pts;        // BVH order: (x, y, z, original id bits)
+    const float4 *by_id;      // original order: (x, y, z, 0)
+    int nrx;
+    float lo[3], hi[3];
+};
+
+// One reception record (64 bytes).
+struct __align__(16) RecDev {
+    int tx, rx, ray, order;
+    int faces[kMaxOrder];
+    float err, dray;
+    int slot, pad;
+};
+
+// Lattice tables for ray generation at division level n.
+struct LatticeDev {
+    const float4 *ico;        // 12 vertices
+    const int2 *edges;        // 30 edges (lo, hi)
+    const float4 *centre;     // 20 face centre directions
+    const float4 *layers;     // [20][nl][3]: (W_e.xyz, angle W_e -> W_{e+1})
+    int n, nl;
+    float edge_angle;         // theta_0
+};
+
+}  // namespace sbr
+
+// ---------------------------------------------------------------- host handle structs
+struct sbr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    sbr_alloc_fn alloc = nullptr;
+    sbr_free_fn free_fn = nullptr;
+    void *user = nullptr;
+    std::string last_error;
+    int num_sms = 0;
+    int max_threads_per_sm = 0;
+    // ray-generation workspace (directions for the last division level)
+    void *dirs = nullptr;
+    size_t dirs_bytes = 0;
+    int dirs_n = 0;
+    bool dirs_valid = false;
+    // lattice tables
+    void *lattice_mem = nullptr;
+    size_t lattice_bytes = 0;
+    int lattice_n = 0;
+    sbr::LatticeDev lattice{};
+    // kernel timing events (SBR_LAUNCH_TIMING)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+struct sbr_scene {
+    void *mem = nullptr;
+    size_t bytes = 0;
+    sbr::SceneDev dev{};
+    sbr_scene_info info{};
+};
+
+struct sbr_rxset {
+    void *mem = nullptr;
+    size_t bytes = 0;
+    sbr::RxDev dev{};
+    std::vector<float> host;   // original order, 3 per receiver
+};
+
+struct sbr_paths {
+    int64_t record_cap = 0, path_cap = 0;
+    void *mem = nullptr;
+    size_t bytes = 0;
+    sbr::RecDev *recs = nullptr;
+    sbr_path_record *paths = nullptr;
+    unsigned long long *table = nullptr;   // dedup hash table: 2 x u64 per slot (key, value)
+    int64_t table_slots = 0;
+    long long *counters = nullptr;         // sbr::kNumCounters
+    int *pair_off = nullptr;               // per-pair path ranges (sbr_refine_pair), lazily sized
+    int64_t pair_cap = 0;
+    void *pair_mem = nullptr;
+    size_t pair_bytes = 0;
+    // launch context kept for refinement
+    float4 *tx = nullptr;                  // device, up to tx_cap transmitters
+    int32_t tx_cap = 0;
+    void *tx_mem = nullptr;
+    size_t tx_bytes = 0;
+    int32_t ntx = 0, nrx = 0, n_div = 0, max_order = 0;
+    const sbr_rxset *rx = nullptr;
+    float alpha = 1.0f;
+    bool timed = false;                    // last launch recorded kernel events
+    int trace_grid = 0, trace_block = 0;
+};
+
+// ---------------------------------------------------------------- internal helpers
+namespace sbr {
+
+// allocation through the context's callbacks (or cudaMallocAsync)
+void *dev_alloc(sbr_ctx *ctx, size_t bytes);
+void dev_free(sbr_ctx *ctx, void *p, size_t bytes);
+
+// host geometry (host_geometry.cpp)
+struct BvhOut {
+    std::vector<float4> nodes;
+    std::vector<int> prim_order;   // BVH leaf order -> original primitive index
+    int depth = 0, max_leaf = 0;
+};
+// Build a binned-SAH BVH over boxes lo/hi (3 floats each) with centroids c.
+bool build_bvh(const std::vector<float> &lo, const std::vector<float> &hi, int leaf_max, BvhOut &out,
+               std::string &err);
+// Lattice layer tables at division level n (host doubles -> float4 table).
+void build_lattice_tables(int n, std::vector<float4> &ico, std::vector<int2> &edges, std::vector<float4> &centre,
+                          std::vector<float4> &layers, int &nl);
+// Sub-ray pattern constants.
+int subray_pattern(int K, double *rho, double *phi, double *shrink);
+
+// kernels (kernels_*.cu)
+cudaError_t launch_raygen(const LatticeDev &lat, float4 *dirs, int64_t N, cudaStream_t s);
+
+struct TraceArgs {
+    SceneDev scene;
+    RxDev rx;
+    const float4 *dirs;
+    const float4 *tx;
+    int ntx;
+    int64_t nrays_per_tx;
+    int max_order;
+    float cone;               // reception cone half-angle (rad)
+    float tan_cone;
+    RecDev *recs;
+    int64_t rec_cap;
+    long long *counters;
+    int dump_stride;
+    int *dump_faces;
+    int64_t dump_per_tx;
+};
+cudaError_t launch_trace(const TraceArgs &a, int grid, int block, cudaStream_t s);
+
+struct DedupArgs {
+    RecDev *recs;
+    int64_t rec_cap;
+    unsigned long long *table;
+    int64_t slots;            // power of two
+    sbr_path_record *paths;
+    int64_t path_cap;
+    const float4 *dirs;       // lattice directions (rough launch direction)
+    long long *counters;
+};
+cudaError_t launch_dedup(const DedupArgs &a, int num_sms, cudaStream_t s);
+
+struct RefineArgs {
+    SceneDev scene;
+    const float4 *tx;
+    const float4 *rx;         // original order
+    sbr_path_record *paths;
+    long long *counters;      // kPaths holds the path count
+    int64_t path_cap;
+    const int *range;         // optional [begin, end) on device (per-pair form), or null
+    const int *index;         // path indices addressed by range (per-pair form)
+    int K;
+    int max_iters;
+    float theta_launch;
+    double target;
+    double fp64_below;
+    double freq;
+    double ptx_dbm;
+    int8_t *choice_log;
+    int chunk;
+    int ntx, nrx, nf;         // bounds of the ids a path record may hold
+};
+cudaError_t launch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s);
+void refine_kernel_attrs(int *regs, int block, int *blocks_per_sm, bool batched);
+cudaError_t upload_subray_table(cudaStream_t s);
+
+struct PairArgs {
+    const sbr_path_record *paths;
+    const long long *counters;
+    int64_t path_cap;
+    int nrx;
+    int npairs;
+    int *pair_count;          // [npairs + 1] scratch: counts then offsets
+    int *pair_idx;            // [path_cap] path indices grouped by pair
+};
+cudaError_t launch_pair_bucket(const PairArgs &a, cudaStream_t s);
+
+struct UnfoldArgs {
+    SceneDev scene;
+    int nf;
+    int64_t n;
+    const float *tx, *rx, *az_el;
+    const int32_t *faces, *order;
+    const float *grad_out;
+    float *out, *grad_tx, *grad_rx, *grad_az_el;
+};
+cudaError_t launch_unfold_fwd(const UnfoldArgs &a, cudaStream_t s);
+cudaError_t launch_unfold_bwd(const UnfoldArgs &a, cudaStream_t s);
+
+int trace_blocks_per_sm(int block);
+
+}  // namespace sbr

@@ -21,6 +21,12 @@ import numpy as np
 SEED_BASE = 2208
 
 
+def f32_exact(a) -> np.ndarray:
+    """Round coordinates to float32 (kept as float64) so that a float32 consumer and a
+    float64 consumer see exactly the same geometry."""
+    return np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
+
+
 @dataclass
 class Scene:
     verts: np.ndarray            # (V, 3) float64
@@ -79,7 +85,7 @@ class _Builder:
         return fid
 
     def finish(self, **meta) -> Scene:
-        v = np.concatenate(self.v).astype(np.float64)
+        v = f32_exact(np.concatenate(self.v))
         t = np.concatenate(self.t).astype(np.int32)
         f = np.concatenate(self.f).astype(np.int32)
         return Scene(v, t, f, self.nf, None, dict(meta))
@@ -130,7 +136,7 @@ def shoebox(L=10.0, W=8.0, H=3.0, g=1) -> Scene:
 def shoebox_config():
     """Shoebox workload: 10 x 8 x 3 m room, Tx (2, 3, 2), Rx (8, 5, 1.5)."""
     sc = shoebox()
-    return sc, np.array([[2.0, 3.0, 2.0]]), np.array([[8.0, 5.0, 1.5]])
+    return sc, f32_exact([[2.0, 3.0, 2.0]]), f32_exact([[8.0, 5.0, 1.5]])
 
 
 # --------------------------------------------------------------------------- urban canyon
@@ -161,7 +167,7 @@ def urban_canyon(seed=SEED_BASE + 2, blocks=20, fmin=20.0, fmax=40.0, street=15.
     sel = street_c[1:17]
     X, Y = np.meshgrid(sel, sel, indexing="ij")
     rx = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 1.5)], -1)
-    return sc, tx, rx
+    return sc, f32_exact(tx), f32_exact(rx)
 
 
 # --------------------------------------------------------------------------- office
@@ -208,7 +214,7 @@ def office(seed=SEED_BASE + 3, nbox=400, ntx=16, nrx=1024, shell=(40.0, 30.0, 4.
 
     tx = free_points(ntx, 2.3, 3.7)
     rx = free_points(nrx, 0.5, 3.5)
-    return sc, tx, rx
+    return sc, f32_exact(tx), f32_exact(rx)
 
 
 # --------------------------------------------------------------------------- large city
@@ -262,9 +268,9 @@ def large_city(seed=SEED_BASE + 5, blocks=60, pitch=55.0, terrain_cells=700, ntx
     sel = np.linspace(street[0], street[-1], side)
     RX, RY = np.meshgrid(sel, street[np.linspace(0, len(street) - 1, side).astype(int)], indexing="ij")
     rx = np.stack([RX.ravel(), RY.ravel(), height(RX, RY).ravel() + 1.5], -1)
-    return sc, tx, rx
+    return sc, f32_exact(tx), f32_exact(rx)
 
 
 def jitter(rng, pts, amount):
-    """Uniform +-amount jitter of every coordinate."""
-    return pts + rng.uniform(-amount, amount, np.shape(pts))
+    """Uniform +-amount jitter of every coordinate (float32-exact)."""
+    return f32_exact(pts + rng.uniform(-amount, amount, np.shape(pts)))

@@ -26,3 +26,15 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gpu_ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_10009_gb300 import api
+    ctx = api.Context(0)
+    yield ctx
+    torch.cuda.synchronize()
+    ctx.close()

@@ -1,0 +1,249 @@
+"""a2-a8 parity on small scenes: per-ray face sequences, rough paths after double-count
+removal, refined paths, validity and outputs, all against the oracle (and the image
+method), through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2208_10009_gb300 import scenes
+
+from parity_util import (EDGE_MARGIN, TOL_ANGLE_RAD, TOL_DELAY_REL, ang, dir_of, gpu_paths_by_key,
+                         oracle_paths_by_key)
+
+pytestmark = pytest.mark.gpu
+SQ3 = float(np.sqrt(3.0))
+
+
+def _setup(gpu_ctx, sc, tx, rx, rec_cap=1 << 16, path_cap=1 << 14):
+    scene = gpu_ctx.scene_from(sc)
+    rxs = gpu_ctx.rx_upload(rx)
+    paths = gpu_ctx.paths_create(rec_cap, path_cap)
+    return scene, rxs, paths
+
+
+def _close(*hs):
+    for h in hs:
+        h.close()
+
+
+def _dump(gpu_ctx, scene, tx, rxs, paths, n, order, alpha, stride):
+    N = 10 * n * n + 2
+    per = (N + stride - 1) // stride
+    dump = torch.full((len(tx), per, order + 1), -3, dtype=torch.int32, device="cuda")
+    gpu_ctx.launch(scene, tx, rxs, paths, n, order, rx_angle_scale=alpha, sync=True, dump_stride=stride, dump=dump)
+    return dump.cpu().numpy()
+
+
+def compare_ray_faces(gpu_faces, ora_faces, margin, min_checked):
+    """Face sequence per ray, rays with edge/grazing margin < EDGE_MARGIN excluded."""
+    keep = margin >= EDGE_MARGIN
+    excluded = int((~keep).sum())
+    mism = np.nonzero(np.any(gpu_faces[keep] != ora_faces[keep], axis=1))[0]
+    assert keep.sum() >= min_checked
+    assert len(mism) == 0, (len(mism), gpu_faces[keep][mism[:5]], ora_faces[keep][mism[:5]])
+    return excluded
+
+
+def test_shoebox_per_ray_trace(gpu_ctx, oracle_mod):
+    sc, tx, rx = scenes.shoebox_config()
+    scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx)
+    n, order = 64, 3
+    d = _dump(gpu_ctx, scene, tx, rxs, paths, n, order, SQ3, 1)[0]
+    S = oracle_mod.Scene.from_generated(sc)
+    tr = oracle_mod.trace(S, tx[0], oracle_mod.lattice(n), rx, order, SQ3 * oracle_mod.theta_launch(n),
+                          want_margin=True)
+    excluded = compare_ray_faces(d, tr.ray_faces, tr.ray_margin, 40000)
+    assert excluded < 100
+    st = gpu_ctx.launch_stats(paths)
+    assert st["segments"] == tr.nsegments == 4 * (10 * n * n + 2)
+    assert st["rays"] == 10 * n * n + 2
+    assert st["collisions"] == 0
+    _close(paths, rxs, scene)
+
+
+def _refine_compare(gpu_ctx, oracle_mod, S, tx, rx, got, n, K, iters, alpha, target=0.0, choice=None):
+    """Compare GPU refined records with the oracle refinement started from the same rough
+    ray.  Returns the number of near-tie divergences."""
+    tl = oracle_mod.theta_launch(n)
+    near_ties = 0
+    for i, r in enumerate(got):
+        k = int(r["order"])
+        faces = tuple(int(f) for f in r["faces"][:k])
+        c0 = oracle_mod.lattice_ids(n, [int(r["ray"])])[0]
+        e0 = oracle_mod.refine(S, tx[r["tx"]], rx[r["rx"]], faces, c0, 1.0, 9, 0)["err"]
+        ref = oracle_mod.refine(S, tx[r["tx"]], rx[r["rx"]], faces, c0, max(tl, e0), K, iters, target)
+        assert int(r["iters"]) == ref["iters"] or target > 0
+        if choice is not None:
+            ch = choice[i, : ref["iters"]]
+            if not np.array_equal(ch, ref["choice"]):
+                near_ties += 1
+                continue
+        assert ang(r["dir"], ref["dir"]) < TOL_ANGLE_RAD, (faces, ang(r["dir"], ref["dir"]))
+        ev = oracle_mod.path_eval(S, tx[r["tx"]], rx[r["rx"]], faces, ref["dir"])
+        assert bool(r["valid"]) == ev["valid"], faces
+        assert abs(r["delay"] / ev["delay"] - 1) < TOL_DELAY_REL
+        assert ang(dir_of(*r["aod"]), dir_of(*ev["aod"])) < TOL_ANGLE_RAD
+        assert ang(dir_of(*r["aoa"]), dir_of(*ev["aoa"])) < TOL_ANGLE_RAD
+        assert abs(r["power_dbm"] - ev["power"]) < 1e-3
+    return near_ties
+
+
+def test_shoebox_paths_refine_and_image_method(gpu_ctx, oracle_mod):
+    """Shoebox workload (10 x 8 x 3 m, n = 64, order 3, alpha = sqrt(3), 5 iterations, K = 9):
+    the 63 image-method paths, GPU == oracle, every AOD within 0.01 deg of IM."""
+    sc, tx, rx = scenes.shoebox_config()
+    scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx)
+    n, order, K, iters = 64, 3, 9, 5
+    gpu_ctx.launch(scene, tx, rxs, paths, n, order, rx_angle_scale=SQ3, sync=True)
+    rough = gpu_ctx.query(paths)
+    S = oracle_mod.Scene.from_generated(sc)
+    ora = oracle_mod.sbr_pipeline(S, tx, rx, n, order, SQ3, K, iters, refine_paths=False)
+    g = gpu_paths_by_key(rough)
+    o = oracle_paths_by_key(ora.paths)
+    assert set(g) == set(o) and len(g) == 63
+    for key, r in g.items():
+        p = o[key]
+        assert abs(r["rough_err"] - p["err"]) < 1e-6
+        if int(r["ray"]) != p["ray"]:
+            # only a near-tie may pick another ray
+            e_other = oracle_mod.refine(S, tx[0], rx[0], key[3], oracle_mod.lattice_ids(n, [int(r["ray"])])[0],
+                                        1.0, 9, 0)["err"]
+            assert abs(e_other - p["err"]) <= 1e-6 * p["err"] + 1e-9
+    choice = torch.full((paths.path_cap, iters), -1, dtype=torch.int8, device="cuda")
+    gpu_ctx.refine(scene, paths, iters, K, choice_log=choice)
+    got = gpu_ctx.query(paths)
+    ch = choice.cpu().numpy()[: len(got)]
+    near = _refine_compare(gpu_ctx, oracle_mod, S, tx, rx, got, n, K, iters, SQ3, choice=ch)
+    assert near <= 2
+    im = {p["faces"]: p for p in oracle_mod.image_enumerate(S, tx[0], rx[0], order)}
+    for r in got:
+        key = tuple(int(f) for f in r["faces"][: r["order"]])
+        assert r["valid"] == 1
+        assert ang(r["dir"], im[key]["aod_dir"]) < 0.01 * np.pi / 180
+    _close(paths, rxs, scene)
+
+
+def test_corridor_two_paths_per_order(gpu_ctx, oracle_mod):
+    W = 4.0
+    sc = scenes.corridor(W)
+    tx, rx = np.array([[0.0, 1.5, 1.0]], np.float32), np.array([[30.0, 2.5, 1.5]], np.float32)
+    scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx)
+    n, order = 48, 5
+    gpu_ctx.launch(scene, tx, rxs, paths, n, order, rx_angle_scale=SQ3, sync=True)
+    gpu_ctx.refine(scene, paths, 12, 9)
+    got = gpu_ctx.query(paths)
+    S = oracle_mod.Scene.from_generated(sc)
+    im = {p["faces"]: p for p in oracle_mod.image_enumerate(S, tx[0], rx[0], order)}
+    keys = {tuple(int(f) for f in r["faces"][: r["order"]]) for r in got if r["valid"]}
+    assert keys == set(im)
+    for r in got:
+        key = tuple(int(f) for f in r["faces"][: r["order"]])
+        assert abs(r["delay"] / im[key]["delay"] - 1) < 1e-6
+        assert ang(r["dir"], im[key]["aod_dir"]) < 0.001 * np.pi / 180
+    _close(paths, rxs, scene)
+
+
+def test_edge_cases(gpu_ctx):
+    from paper_2208_10009_gb300 import api
+    sc, tx, rx = scenes.shoebox_config()
+    scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx)
+    # LOS only
+    gpu_ctx.launch(scene, tx, rxs, paths, 8, 0, rx_angle_scale=SQ3, sync=True)
+    got = gpu_ctx.query(paths)
+    assert len(got) == 1 and got[0]["order"] == 0
+    assert gpu_ctx.launch_stats(paths)["segments"] == 10 * 64 + 2
+    # n = 1: the 12 icosahedron vertices only
+    gpu_ctx.launch(scene, tx, rxs, paths, 1, 3, rx_angle_scale=SQ3, sync=True)
+    assert gpu_ctx.launch_stats(paths)["segments"] == 12 * 4
+    # no receivers
+    empty_rx = gpu_ctx.rx_upload(np.zeros((0, 3), np.float32))
+    gpu_ctx.launch(scene, tx, empty_rx, paths, 8, 2, rx_angle_scale=SQ3, sync=True)
+    assert gpu_ctx.paths_count(paths) == 0
+    gpu_ctx.refine(scene, paths, 3, 9)
+    # record overflow is reported, never written past the buffer
+    tiny = gpu_ctx.paths_create(2, 2)
+    with pytest.raises(api.SbrError) as e:
+        gpu_ctx.launch(scene, tx, rxs, tiny, 64, 3, rx_angle_scale=SQ3, sync=True)
+    assert e.value.status == 5
+    st = gpu_ctx.launch_stats(tiny)
+    assert st["records"] > 2
+    # bad arguments
+    for kw in (dict(n_div=0, max_order=2), dict(n_div=8, max_order=9)):
+        with pytest.raises(api.SbrError):
+            gpu_ctx.launch(scene, tx, rxs, paths, kw["n_div"], kw["max_order"])
+    with pytest.raises(api.SbrError):
+        gpu_ctx.refine(scene, paths, 3, 8)
+    _close(tiny, empty_rx, paths, rxs, scene)
+
+
+def test_degenerate_scenes_rejected(gpu_ctx):
+    from paper_2208_10009_gb300 import api
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    with pytest.raises(api.SbrError) as e:
+        gpu_ctx.scene_upload(np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0]], np.float32), [[0, 1, 2]], [0])
+    assert e.value.status == 6
+    bad = v.copy()
+    bad[1, 0] = np.nan
+    with pytest.raises(api.SbrError):
+        gpu_ctx.scene_upload(bad, [[0, 1, 2]], [0])
+    with pytest.raises(api.SbrError):
+        gpu_ctx.scene_upload(v, [[0, 1, 5]], [0])
+    with pytest.raises(api.SbrError):
+        gpu_ctx.scene_upload(v, [[0, 1, 2]], [3], nf=1)
+
+
+def test_empty_scene_only_los(gpu_ctx, oracle_mod):
+    scene = gpu_ctx.scene_upload(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), np.zeros(0, np.int32), nf=0)
+    tx, rx = np.array([[0, 0, 0]], np.float32), np.array([[5, 1, 2]], np.float32)
+    rxs = gpu_ctx.rx_upload(rx)
+    paths = gpu_ctx.paths_create(1024, 64)
+    gpu_ctx.launch(scene, tx, rxs, paths, 16, 4, rx_angle_scale=SQ3, sync=True)
+    gpu_ctx.refine(scene, paths, 10, 9)
+    got = gpu_ctx.query(paths)
+    assert len(got) == 1 and got[0]["order"] == 0 and got[0]["valid"] == 1
+    assert abs(got[0]["delay"] * 299792458.0 / np.linalg.norm(rx[0] - tx[0]) - 1) < 1e-6
+    assert gpu_ctx.launch_stats(paths)["segments"] == 10 * 256 + 2
+    _close(paths, rxs, scene)
+
+
+def test_batched_and_per_pair_equal_plain(gpu_ctx):
+    """a9: the persistent work-queue form and the per-pair form give the plain form's
+    results (same device arithmetic, different schedule)."""
+    sc, tx, rx = scenes.office(nbox=60, ntx=2, nrx=12, g_shell=8, g_box=1)
+    scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx, 1 << 18, 1 << 16)
+    res = []
+    for mode in ("plain", "batch", "pair"):
+        gpu_ctx.launch(scene, tx, rxs, paths, 48, 3, rx_angle_scale=SQ3, sync=True)
+        if mode == "plain":
+            gpu_ctx.refine(scene, paths, 8, 16, target=np.radians(0.01))
+        elif mode == "batch":
+            gpu_ctx.batch_refine(scene, paths, 8, 16, target=np.radians(0.01), chunk=2)
+        else:
+            for t in range(len(tx)):
+                for r in range(len(rx)):
+                    gpu_ctx.refine_pair(scene, paths, t, r, 8, 16, target=np.radians(0.01))
+        got = gpu_ctx.query(paths)
+        res.append({(int(g["tx"]), int(g["rx"]), int(g["order"]), tuple(g["faces"])): g for g in got})
+    assert len(res[0]) > 50
+    for other in res[1:]:
+        assert set(other) == set(res[0])
+        for k, g in res[0].items():
+            h = other[k]
+            assert g["iters"] == h["iters"] and g["valid"] == h["valid"]
+            assert ang(g["dir"], h["dir"]) < 1e-9
+            assert abs(g["delay"] - h["delay"]) <= 1e-12 * g["delay"]
+    _close(paths, rxs, scene)
+
+
+def test_repeatable(gpu_ctx):
+    """Two launches + refinements of the same inputs give identical records."""
+    sc, tx, rx = scenes.shoebox_config()
+    scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx)
+    runs = []
+    for _ in range(3):
+        gpu_ctx.launch(scene, tx, rxs, paths, 24, 2, rx_angle_scale=SQ3, sync=True)
+        gpu_ctx.refine(scene, paths, 5, 9)
+        got = gpu_ctx.query(paths)
+        runs.append({(int(g["order"]), tuple(g["faces"])): g.tobytes() for g in got})
+    assert runs[0] == runs[1] == runs[2]
+    _close(paths, rxs, scene)

@@ -1,0 +1,78 @@
+"""CPU checks of the CUDA library's boundary: it builds, loads without a GPU, exports
+every entry point declared in include/sbr.h, and its host-only functions agree with the
+paper's closed forms."""
+import os
+import re
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sbr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(sbr_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_10009_gb300 import _binding
+    return _binding.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2208_10009_gb300 import _binding
+    names = _declared()
+    assert len(names) >= 28
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _binding.SIGNATURES, n
+
+
+def test_host_functions(lib):
+    from paper_2208_10009_gb300 import api
+    assert lib.sbr_abi_version() == 1
+    assert lib.sbr_status_string(0) == b"ok"
+    for n in (1, 2, 21, 64, 700, 2200):
+        assert api.num_rays(n) == 10 * n * n + 2
+    assert api.num_rays(0) == -1
+    th0 = np.arccos(1 / np.sqrt(5))
+    for n in (1, 21, 700):
+        assert abs(api.theta_launch(n) - th0 / (np.sqrt(3) * n)) < 1e-15
+
+
+@pytest.mark.parametrize("K", [6, 7, 9, 16])
+def test_library_subray_patterns_cover(K):
+    """The library's own sub-ray constants cover the cone with their shrink factor."""
+    from paper_2208_10009_gb300 import api
+    rho, phi, s = api.subray_pattern(K)
+    C = np.stack([rho * np.cos(phi), rho * np.sin(phi)], -1)
+    rng = np.random.default_rng(100 + K)
+    p = rng.uniform(-1, 1, (400000, 2))
+    p = p[(p ** 2).sum(1) <= 1]
+    t = np.linspace(0, 2 * np.pi, 20000, endpoint=False)
+    p = np.vstack([p, np.c_[np.cos(t), np.sin(t)]])
+    d, _ = cKDTree(C).query(p)
+    assert d.max() <= s * (1 + 1e-9)
+    if K == 6:
+        assert abs(s - 1 / np.sqrt(3)) < 1e-15
+
+
+def test_bad_pattern_rejected():
+    from paper_2208_10009_gb300 import api
+    with pytest.raises(api.SbrError):
+        api.subray_pattern(8)
+
+
+def test_oracle_not_imported_by_product():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2208_10009_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "sbr_oracle" not in txt, f
