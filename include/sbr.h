@@ -260,6 +260,32 @@ sbr_status sbr_unfold_bwd(sbr_ctx *ctx, const sbr_scene *scene, int64_t npaths, 
                           const float *rx, const float *az_el, const int32_t *faces, const int32_t *order,
                           const float *grad_out, float *grad_tx, float *grad_rx, float *grad_az_el);
 
+/* ---------------------------------------------------------------- allocation-free dedup */
+/* The paper has no counterpart of this entry point; it serves callers that cannot let the
+ * library allocate: code being captured into a CUDA graph (cudaMalloc / cudaFree are not
+ * allowed during stream capture) and processes whose device memory is fully reserved by
+ * another framework's pool.
+ *
+ * sbr_dedup_noalloc repeats the double-count removal of sbr_launch on the reception
+ * records that the last sbr_launch left in `src`, writing the unique paths to `out`
+ * (DEVICE, room for `cap` records, filled in unspecified order like sbr_query's) and
+ * counts[0] = number of unique paths (may exceed cap; only cap are written),
+ * counts[1] = hash collisions detected (0 when correct) to `counts` (DEVICE, 2 int64).
+ * It allocates and frees nothing: its hash table is a fixed array of about 5.5 MiB in
+ * device global memory that every GPU loading the library keeps until the process exits.
+ * Limits and rules:
+ *   - SBR_EINVAL if src's record capacity exceeds SBR_NOALLOC_MAX_RECORDS, or if the
+ *     context's ray directions no longer belong to src's launch (another division level
+ *     was launched since);
+ *   - all calls share the array; each call clears it first, and calls whose GPU work
+ *     overlaps (e.g. on two streams) race and corrupt each other's output;
+ *   - the first call on a device looks up the array's device address for that device;
+ *     make that first call before any stream capture.
+ * Asynchronous on the context's stream. */
+#define SBR_NOALLOC_MAX_RECORDS 131072
+sbr_status sbr_dedup_noalloc(sbr_ctx *ctx, const sbr_paths *src, sbr_path_record *out, int64_t cap,
+                             int64_t *counts);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,7 @@ SIGNATURES = {
     "sbr_paths_import": (_i32, [_vp, _vp, _vp, _i64, _vp, _i32, _vp, _i32]),
     "sbr_unfold_fwd": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sbr_unfold_bwd": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sbr_dedup_noalloc": (_i32, [_vp, _vp, _vp, _i64, _vp]),
 }
 
 _lib = None
