@@ -729,8 +729,10 @@ static double fresnel_perp(double ci, double eps) {
 /*
  * Validity test and channel outputs of one path for launch direction `dir` (§III.A
  * second path test; §IV outputs).  The bounce points p_1..p_k are recomputed through the
- * fixed planes; the path is valid iff every p_i lies in its face and no segment
- * Tx->p_1->...->p_k->Rx is blocked (endpoint faces excluded).  Outputs: delay = polyline
+ * fixed planes; the path is valid iff every p_i lies in its face, the foot of Rx on the
+ * last leg lies ahead of the last bounce point (the reception judgment's condition that
+ * Rx is received on that segment, §III.A/B), and no segment Tx->p_1->...->p_k->Rx is
+ * blocked (endpoint faces excluded).  Outputs: delay = polyline
  * length to the exact Rx / c0; AOD = (azimuth, elevation) of dir; AOA = (azimuth,
  * elevation) of p_k - Rx (Tx - Rx for LOS); power (dBm) = ptx + 20 log10(lambda / (4 pi
  * length)) + sum 20 log10 |Gamma_perp| (parity unpinned beyond one plane); err = Eq. 3
@@ -775,6 +777,8 @@ int ora_path_eval(void *sp, const double *tx3, const double *rx3, int order, con
         }
         prev = nxt;
     }
+    /* dd is now the direction of the last leg */
+    if (dot(sub(rx, order > 0 ? P[order - 1] : tx), dd) <= 0.0) ok = 0;
     *valid = ok;
     *delay = len / ORA_C0;
     az_el(d, aod);
