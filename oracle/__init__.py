@@ -77,7 +77,7 @@ def _load():
             "ora_refine": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, _d, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, _d, _d, _i32, _d]),
             "ora_path_eval": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, _d, ctypes.c_double,
-                                             ctypes.c_double, _d, _i32, _d, _d, _d, _d, _d]),
+                                             ctypes.c_double, ctypes.c_double, _d, _i32, _d, _d, _d, _d, _d]),
             "ora_image_path": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, ctypes.c_double,
                                               ctypes.c_double, _d, _d, _d, _d, _d, _d]),
             "ora_image_enumerate": (ctypes.c_int64, [_vp, _d, _d, ctypes.c_int, ctypes.c_int64, _i32, _i32,
@@ -289,15 +289,24 @@ def refine(scene: Scene, tx, rx, faces, c0, R0: float, K: int, iters: int, targe
     return dict(dir=out_dir, err=float(out_err[0]), iters=it, choice=choice[:it], err_hist=hist[: it + 1])
 
 
-def path_eval(scene: Scene, tx, rx, faces, direction, freq=2.4e9, ptx_dbm=0.0):
-    """Validity test and outputs of one path launched along ``direction``."""
+def refined_err_bound(R0: float, K: int, iters: int) -> float:
+    """Twice the Eq. 10 bound after ``iters`` iterations plus the FP32 evaluation floor: the
+    error angle a refined path must not exceed to count as converged."""
+    _, _, s = subray_pattern(K)
+    return 2.0 * R0 * s ** iters + 1e-7
+
+
+def path_eval(scene: Scene, tx, rx, faces, direction, freq=2.4e9, ptx_dbm=0.0, err_bound=0.0):
+    """Validity test and outputs of one path launched along ``direction`` (err_bound > 0
+    adds the convergence condition, see ``ora_path_eval``)."""
     fa = _faces_arr(faces)
     pts = np.zeros((MAX_ORDER, 3))
     valid = np.zeros(1, np.int32)
     delay, power, err = np.zeros(1), np.zeros(1), np.zeros(1)
     aod, aoa = np.zeros(2), np.zeros(2)
     r = _load().ora_path_eval(scene.handle, _p(_f64(tx, (3,))), _p(_f64(rx, (3,))), len(faces), _p(fa, _i32),
-                              _p(_f64(direction, (3,))), freq, ptx_dbm, _p(pts), _p(valid, _i32), _p(delay),
+                              _p(_f64(direction, (3,))), freq, ptx_dbm, err_bound, _p(pts), _p(valid, _i32),
+                              _p(delay),
                               _p(aod), _p(aoa), _p(power), _p(err))
     return dict(ok=(r == 0), valid=bool(valid[0]), points=pts[: len(faces)], delay=float(delay[0]), aod=aod,
                 aoa=aoa, power=float(power[0]), err=float(err[0]))
@@ -390,7 +399,8 @@ def sbr_pipeline(scene: Scene, txs, rxs, n: int, max_order: int, alpha: float, K
                 r = refine(scene, tx, rxs[p["rx"]], p["faces"], c0, R0, K, iters, target)
                 p.update(ref_dir=r["dir"], ref_err=r["err"], iters=r["iters"], choice=r["choice"],
                          err_hist=r["err_hist"])
-                ev = path_eval(scene, tx, rxs[p["rx"]], p["faces"], r["dir"], freq)
+                bound = refined_err_bound(R0, K, r["iters"]) if r["iters"] > 0 else 0.0
+                ev = path_eval(scene, tx, rxs[p["rx"]], p["faces"], r["dir"], freq, err_bound=bound)
                 p.update(valid=ev["valid"], delay=ev["delay"], aod=ev["aod"], aoa=ev["aoa"], power=ev["power"],
                          points=ev["points"])
             paths.append(p)

@@ -313,12 +313,21 @@ int ora_subray_pattern(int K, double *rho, double *phi, double *shrink) {
         }
         *shrink = r;
     } else if (K == 16) {
-        double lo = 0.30, hi = 0.36, r5 = 0, r10 = 0;
-        for (int it = 0; it < 60; ++it) {
-            double mid = 0.5 * (lo + hi), a, b;
-            if (k16_feasible(mid, &a, &b)) hi = mid; else lo = mid;
+        /* the search is deterministic; computed once per process */
+        static double c_hi = 0, c_r5 = 0, c_r10 = 0;
+        static int done = 0;
+#pragma omp critical(ora_k16)
+        if (!done) {
+            double lo = 0.30, h = 0.36, a, b;
+            for (int it = 0; it < 60; ++it) {
+                double mid = 0.5 * (lo + h);
+                if (k16_feasible(mid, &a, &b)) h = mid; else lo = mid;
+            }
+            k16_feasible(h, &c_r5, &c_r10);
+            c_hi = h;
+            done = 1;
         }
-        k16_feasible(hi, &r5, &r10);
+        double hi = c_hi, r5 = c_r5, r10 = c_r10;
         rho[k] = 0; phi[k] = 0; ++k;
         for (int j = 0; j < 5; ++j) { rho[k] = r5; phi[k] = 2.0 * M_PI / 5.0 * j; ++k; }
         for (int j = 0; j < 10; ++j) { rho[k] = r10; phi[k] = 2.0 * M_PI / 10.0 * j; ++k; }
@@ -731,16 +740,21 @@ static double fresnel_perp(double ci, double eps) {
  * second path test; §IV outputs).  The bounce points p_1..p_k are recomputed through the
  * fixed planes; the path is valid iff every p_i lies in its face, the foot of Rx on the
  * last leg lies ahead of the last bounce point (the reception judgment's condition that
- * Rx is received on that segment, §III.A/B), and no segment Tx->p_1->...->p_k->Rx is
- * blocked (endpoint faces excluded).  Outputs: delay = polyline
+ * Rx is received on that segment, §III.A/B), no segment Tx->p_1->...->p_k->Rx is
+ * blocked (endpoint faces excluded), and -- when err_bound > 0 -- the error angle of dir is
+ * at most err_bound.  The caller passes twice the Eq. 10 bound of the refinement that
+ * produced dir (plus the FP32 evaluation floor): a path whose exact direction lies in its
+ * cone always meets the bound, while a redundant path received through the cone's width
+ * for a face sequence with no specular solution stalls far above it (§III.A: such paths
+ * are removed after the precise algorithm).  Outputs: delay = polyline
  * length to the exact Rx / c0; AOD = (azimuth, elevation) of dir; AOA = (azimuth,
  * elevation) of p_k - Rx (Tx - Rx for LOS); power (dBm) = ptx + 20 log10(lambda / (4 pi
  * length)) + sum 20 log10 |Gamma_perp| (parity unpinned beyond one plane); err = Eq. 3
  * error angle of dir.  Returns 0, or -1 if the fixed-plane trace fails.
  */
 int ora_path_eval(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
-                  const double *dir, double freq, double ptx_dbm, double *pts_out, int32_t *valid,
-                  double *delay, double *aod, double *aoa, double *power, double *err) {
+                  const double *dir, double freq, double ptx_dbm, double err_bound, double *pts_out,
+                  int32_t *valid, double *delay, double *aod, double *aoa, double *power, double *err) {
     const scene *s = (const scene *)sp;
     vec3 tx = ld(tx3), rx = ld(rx3), d = unit(ld(dir));
     vec3 P[ORA_MAX_ORDER];
@@ -779,6 +793,7 @@ int ora_path_eval(void *sp, const double *tx3, const double *rx3, int order, con
     }
     /* dd is now the direction of the last leg */
     if (dot(sub(rx, order > 0 ? P[order - 1] : tx), dd) <= 0.0) ok = 0;
+    if (err_bound > 0.0 && !(e <= err_bound)) ok = 0;
     *valid = ok;
     *delay = len / ORA_C0;
     az_el(d, aod);

@@ -119,3 +119,21 @@ def test_brute_force_room_with_pillar(oracle_mod):
     assert len(valid) >= 0.9 * len(im)
     for f, p in valid.items():
         assert abs(p["delay"] / im[f]["delay"] - 1) < 1e-9
+
+
+def test_validity_removes_redundant_paths(oracle_mod):
+    """§III.A: redundant paths received through the cone's width are removed after the
+    precise algorithm.  In a cluttered room, every path the pipeline keeps is a valid
+    image-method path, and every rejected one that the image method rejects too."""
+    sc, tx, rx = scenes.office(nbox=40, ntx=1, nrx=3, g_shell=2, g_box=1)
+    S = oracle_mod.Scene.from_generated(sc)
+    res = oracle_mod.sbr_pipeline(S, tx, rx, 32, 4, np.sqrt(3), 16, 8)
+    kept = rejected_real = 0
+    for p in res.paths:
+        im = oracle_mod.image_path(S, tx[0], rx[p["rx"]], p["faces"])
+        if p["valid"]:
+            assert im["valid"], p["faces"]
+            kept += 1
+        else:
+            rejected_real += im["valid"]
+    assert kept > 200 and rejected_real <= 2
