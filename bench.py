@@ -149,7 +149,7 @@ def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2208_10009_gb300 import api, scenes
+    from paper_2208_10009_gb300 import api, autotune, scenes
 
     rank, world, local = _dist_env()
     if world > 1:
@@ -172,9 +172,16 @@ def run_gpu(args):
     paths = ctx.paths_create(max(2 * st0["records"], 1024), max(2 * st0["paths"], 256))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    # pick the batched kernel's launch shape on these paths (autotuner)
+    def relaunch():
+        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha)
+
+    tuned = autotune.tune_batch_refine(ctx, scene, paths, relaunch, iters, K)
+    shape = {k: tuned[k] for k in ("block_threads", "lanes_per_path", "blocks_per_sm")}
+
     def step():
         ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha)
-        ctx.batch_refine(scene, paths, iters, K)
+        ctx.batch_refine(scene, paths, iters, K, **shape)
 
     # one timed (event) launch to split the step into kernels
     for _ in range(2):
@@ -182,7 +189,7 @@ def run_gpu(args):
     ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, timing=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ctx.batch_refine(scene, paths, iters, K)
+    ctx.batch_refine(scene, paths, iters, K, **shape)
     e1.record(stream)
     torch.cuda.synchronize()
     st_t = ctx.launch_stats(paths)
@@ -235,9 +242,9 @@ def run_gpu(args):
 
     # the batched graph form vs the plain per-pair launch-and-refine form
     per_pair_ms = _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, len(rx))
-    batch_ms = _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream)
+    batch_ms = _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream, shape)
 
-    e2e = _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args)
+    e2e = _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape)
 
     out = {"metric": METRIC, "value": value, "unit": "ray-bounces/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -253,6 +260,7 @@ def run_gpu(args):
                          "batch_refine": ms_refine},
            "trace_counters": {k: st_t[k] for k in ("node_visits", "tri_tests", "rx_tests", "records", "segments")},
            "refine_batched_graph_ms": batch_ms, "refine_per_pair_ms": per_pair_ms,
+           "batch_refine_shape": dict(shape, tuned_ms=tuned["ms"]),
            "roofline": {"bound": "alu", "kernel": "trace_kernel", "achieved": achieved, "peak": peak_tflops,
                         "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} MEASURED_PEAKS.json)",
@@ -297,34 +305,42 @@ def _count_accurate(ctx, scene, tx, rx, recs):
     return int(ok.sum())
 
 
-def _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, nrx):
+def _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, nrx, trials=3):
+    """The plain per-pair form: one refinement launch per (Tx, Rx) pair from the host,
+    each on the same fresh rough paths as the batched form."""
     import torch
     ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
-    ctx.refine_pair(scene, paths, 0, 0, iters, K)   # builds the pair buckets
-    torch.cuda.synchronize()
-    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
-    t = time.perf_counter()
-    for r in range(nrx):
-        ctx.refine_pair(scene, paths, 0, r, iters, K)
-    torch.cuda.synchronize()
-    return 1e3 * (time.perf_counter() - t)
+    ctx.refine_pair(scene, paths, 0, 0, iters, K)   # builds the per-pair buckets
+    out = []
+    for _ in range(trials):
+        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+        t = time.perf_counter()
+        for r in range(nrx):
+            ctx.refine_pair(scene, paths, 0, r, iters, K)
+        torch.cuda.synchronize()
+        out.append(1e3 * (time.perf_counter() - t))
+    return float(np.median(out))
 
 
-def _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream):
+def _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream, shape, trials=3):
+    """The batched form: one graph-captured persistent refinement launch for all pairs,
+    timed on the host like the per-pair form, on fresh rough paths each trial."""
     import torch
     ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
-        ctx.batch_refine(scene, paths, iters, K)
-    g.replay()
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    g.replay()
-    torch.cuda.synchronize()
-    return 1e3 * (time.perf_counter() - t)
+        ctx.batch_refine(scene, paths, iters, K, **shape)
+    out = []
+    for _ in range(trials):
+        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+        t = time.perf_counter()
+        g.replay()
+        torch.cuda.synchronize()
+        out.append(1e3 * (time.perf_counter() - t))
+    return float(np.median(out))
 
 
-def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args):
+def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape):
     """Same step through the C ABI with host inputs: Tx/Rx from pinned host memory (the
     receiver BVH is rebuilt from them), results read back to pinned host memory."""
     import torch
@@ -339,7 +355,7 @@ def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args):
         nonlocal nbytes_out
         rxs = ctx.rx_upload(rx_h)
         ctx.launch(scene, tx_h, rxs, paths, n, order, rx_angle_scale=alpha)
-        ctx.batch_refine(scene, paths, iters, K)
+        ctx.batch_refine(scene, paths, iters, K, **shape)
         got = ctx.query(paths, out_h)
         nbytes_out = len(got) * 128
         rxs.close()

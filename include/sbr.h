@@ -198,13 +198,15 @@ sbr_status sbr_refine_pair(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *path
 typedef struct {
     int32_t block_threads;   /* threads per block (0 = 128) */
     int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid (0 = max) */
-    int32_t chunk;           /* paths a warp takes from the queue per grab (0 = 32) */
+    int32_t lanes_per_path;  /* lanes cooperating on one path: 8, 16 or 32 (0 = 16) */
 } sbr_batch_config;
 
 /* a9 -- batched form of a6-a8: one persistent launch refines all paths of all (Tx, Rx)
- * pairs; warps take chunks of paths from a device work queue (atomic head), so paths
- * that stop early (target reached) free their lanes for new ones.  Capturable in a CUDA
- * graph (no host synchronisation, no allocation after the first call per container). */
+ * pairs.  A group of lanes_per_path lanes owns one path: its lanes evaluate the K
+ * sub-rays of an iteration in parallel and share the validity queries; a group that
+ * finishes a path (iteration cap, target reached) takes the next one from a device work
+ * queue (atomic head), so uneven iteration counts do not idle the GPU.  Results equal
+ * sbr_refine's.  Capturable in a CUDA graph (no host synchronisation, no allocation). */
 sbr_status sbr_batch_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths,
                             const sbr_refine_params *params, const sbr_batch_config *cfg);
 

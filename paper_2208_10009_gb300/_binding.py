@@ -53,7 +53,7 @@ class RefineParams(_c.Structure):
 
 
 class BatchConfig(_c.Structure):
-    _fields_ = [("block_threads", _i32), ("blocks_per_sm", _i32), ("chunk", _i32)]
+    _fields_ = [("block_threads", _i32), ("blocks_per_sm", _i32), ("lanes_per_path", _i32)]
 
 
 LAUNCH_SYNC = 1

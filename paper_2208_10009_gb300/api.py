@@ -216,10 +216,10 @@ class Context:
 
     def batch_refine(self, scene: Scene, paths: Paths, max_iters: int, subrays: int = 9, target: float = 0.0,
                      fp64_below: float = 1e-5, freq: float = 2.4e9, ptx_dbm: float = 0.0, choice_log=None,
-                     block_threads: int = 0, blocks_per_sm: int = 0, chunk: int = 0):
+                     block_threads: int = 0, blocks_per_sm: int = 0, lanes_per_path: int = 0):
         """a9: persistent work-queue refinement of all pairs' paths in one launch."""
         prm = self._refine_params(max_iters, subrays, target, fp64_below, freq, ptx_dbm, choice_log)
-        cfg = B.BatchConfig(block_threads, blocks_per_sm, chunk)
+        cfg = B.BatchConfig(block_threads, blocks_per_sm, lanes_per_path)
         self._check(self.lib.sbr_batch_refine(self.handle, scene.handle, paths.handle, ctypes.byref(prm),
                                               ctypes.byref(cfg)))
 

@@ -572,7 +572,8 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     a.dump_faces = prm->dump_faces;
     a.dump_per_tx = prm->dump_stride > 0 ? (N + prm->dump_stride - 1) / prm->dump_stride : 0;
     int block = prm->block_threads > 0 ? prm->block_threads : 128;
-    if (block % 32 != 0 || block > 1024) return fail(ctx, SBR_EINVAL, "sbr_launch: block_threads must be a multiple of 32");
+    if (block % 32 != 0 || block > 256)
+        return fail(ctx, SBR_EINVAL, "sbr_launch: block_threads must be a multiple of 32, at most 256");
     int grid = prm->grid_blocks > 0 ? prm->grid_blocks : ctx->num_sms * trace_blocks_per_sm(block);
     SBR_CUDA(launch_trace(a, grid, block, ctx->stream));
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
@@ -676,7 +677,7 @@ sbr_status sbr_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths, co
     if (st != SBR_OK) return st;
     DeviceGuard g(ctx->device);
     int nb = 1;
-    refine_kernel_attrs(nullptr, 128, &nb, false);
+    refine_kernel_attrs(nullptr, 128, &nb, false, 0);
     SBR_CUDA(launch_refine(A, ctx->num_sms * nb, 128, ctx->stream));
     return SBR_OK;
 }
@@ -729,11 +730,15 @@ sbr_status sbr_batch_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *pat
     if (st != SBR_OK) return st;
     DeviceGuard g(ctx->device);
     int block = cfg && cfg->block_threads > 0 ? cfg->block_threads : 128;
-    if (block % 32 != 0 || block > 1024) return fail(ctx, SBR_EINVAL, "sbr_batch_refine: block_threads must be a multiple of 32");
+    if (block % 32 != 0 || block > 256)
+        return fail(ctx, SBR_EINVAL, "sbr_batch_refine: block_threads must be a multiple of 32, at most 256");
+    int lanes = cfg && cfg->lanes_per_path > 0 ? cfg->lanes_per_path : 16;
+    if (lanes != 8 && lanes != 16 && lanes != 32)
+        return fail(ctx, SBR_EINVAL, "sbr_batch_refine: lanes_per_path must be 8, 16 or 32");
     int nb = 1;
-    refine_kernel_attrs(nullptr, block, &nb, true);
+    refine_kernel_attrs(nullptr, block, &nb, true, lanes);
     if (cfg && cfg->blocks_per_sm > 0) nb = std::min(nb, cfg->blocks_per_sm);
-    A.chunk = cfg && cfg->chunk > 0 ? cfg->chunk : 1;
+    A.chunk = lanes;
     SBR_CUDA(launch_batch_refine(A, ctx->num_sms * nb, block, ctx->stream));
     return SBR_OK;
 }

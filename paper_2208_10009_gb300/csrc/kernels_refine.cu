@@ -255,8 +255,16 @@ __device__ __forceinline__ void az_el(dvec3 v, float *out) {
     out[1] = (float)atan2(v.z, sqrt(v.x * v.x + v.y * v.y));
 }
 
+// Upper bound on the final error angle of a refined path whose exact direction lies in
+// its cone: twice the Eq. 10 bound R0 * s^iters (R_final) plus the FP32 evaluation floor.
+// A redundant path received through the cone's width for a face sequence without a
+// specular solution stalls far above it and is rejected by the validity test.
+__device__ __forceinline__ double converged_bound(int iters, double R_final) {
+    return iters > 0 ? 2.0 * R_final + 1e-7 : INFINITY;
+}
+
 // Validity test and outputs for launch direction c; writes the result fields of p.
-__device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sbr_path_record &p) {
+__device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sbr_path_record &p, double err_bound) {
     const SceneDev &S = A.scene;
     dvec3 pts[kMaxOrder];
     dvec3 o = g.txd, d = c;
@@ -284,7 +292,9 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
         p.delay = 0.0;
         return;
     }
-    bool valid = true;
+    // Rx must be received on the last leg (its foot lies ahead of the last bounce point)
+    // and the refinement must have converged
+    bool valid = ddot(g.rxd - o, d) > 0.0 && p.err <= err_bound;
     for (int j = 0; j < g.k && valid; ++j) valid = point_in_face(S, g.faces[j], pts[j]);
     double len = 0.0;
     for (int j = 0; j <= g.k; ++j) {
@@ -331,7 +341,7 @@ __device__ __forceinline__ long long path_count(const RefineArgs &A) {
 }
 
 // a6-a8, one thread per path (static grid-stride schedule).
-__global__ void __launch_bounds__(128) refine_kernel(RefineArgs A) {
+__global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
     const long long total = A.range ? (long long)(A.range[1] - A.range[0]) : path_count(A);
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
@@ -373,106 +383,238 @@ __global__ void __launch_bounds__(128) refine_kernel(RefineArgs A) {
         p.dir[1] = c.y;
         p.dir[2] = c.z;
         p.err = err;
-        finalize_path(A, g, c, p);
+        finalize_path(A, g, c, p, converged_bound(it, R));
         store_result(A.paths + pi, p);
     }
 }
 
-// a9: persistent work-queue form.  Each lane owns one path at a time and advances it by
-// up to `chunk` iterations per step; lanes whose path is finished run its validity test
-// and outputs and take new path indices from the queue head (one atomic per warp via
-// ballot/popc), so lanes freed by early-stopping paths are refilled at once.
-__global__ void __launch_bounds__(128) batch_refine_kernel(RefineArgs A) {
-    const long long total = path_count(A);
-    const int off = c_sub.off[A.K];
-    const double shrink = c_sub.shrink[A.K];
-    const unsigned lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
-    long long pi = -1;
-    bool empty = false;
-    sbr_path_record p;
-    PathGeo g;
-    dvec3 c = dv(0, 0, 0);
-    double R = 0, err = 0;
-    int it = 0, flags = 0;
-    bool done = false;
-    for (;;) {
-        unsigned need = __ballot_sync(0xffffffffu, pi < 0);
-        if (need && !empty) {
-            unsigned long long base = 0;
-            if (lane == 0)
-                base = atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kBatchHead),
-                                 (unsigned long long)__popc(need));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if ((long long)base >= total) empty = true;
-            if (pi < 0) {
-                long long q = (long long)base + __popc(need & lt);
-                if (q < total) {
-                    pi = q;
-                    p = A.paths[pi];
-                    if (!path_ids_ok(A, p)) {
-                        A.paths[pi].valid = 0;
-                        A.paths[pi].flags = SBR_PATH_TRACE_FAIL;
-                        pi = -1;
-                    }
-                }
-                if (pi >= 0) {
-                    load_path(A, p, g);
-                    c = dv(p.dir[0], p.dir[1], p.dir[2]);
-                    R = fmax((double)A.theta_launch, (double)p.rough_err);
-                    err = R < A.fp64_below ? eval64(A.scene, g, c)
-                                           : (double)eval32(A.scene, g, make_float3((float)c.x, (float)c.y, (float)c.z));
-                    it = 0;
-                    flags = 0;
-                    done = false;
-                }
-            }
-        }
-        if (__ballot_sync(0xffffffffu, pi >= 0) == 0) break;
-        if (pi < 0) continue;
-        for (int step = 0; step < A.chunk && !done; ++step) {
-            if (!(it < A.max_iters && !(A.target > 0.0 && err <= A.target))) {
-                done = true;
-                break;
-            }
-            int bk;
-            if (R < A.fp64_below) {
-                bk = iterate64(A.scene, g, A.K, off, R, c, err);
-                flags |= SBR_PATH_FP64;
-            } else {
-                bk = iterate32(A.scene, g, A.K, off, R, c, err);
-            }
-            if (bk < 0) {
-                flags |= SBR_PATH_TRACE_FAIL;
-                done = true;
-                break;
-            }
-            if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
-            R *= shrink;
-            ++it;
-        }
-        if (!done && !(it < A.max_iters && !(A.target > 0.0 && err <= A.target))) done = true;
-        if (done) {
-            p.iters = it;
-            p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
-            p.dir[0] = c.x;
-            p.dir[1] = c.y;
-            p.dir[2] = c.z;
-            p.err = err;
-            finalize_path(A, g, c, p);
-            store_result(A.paths + pi, p);
-            pi = -1;
+// a9: persistent work-queue form.  A group of G lanes (G = 8, 16 or 32) owns one path at a
+// time: lane l evaluates the sub-rays k = l, l + G, ... of each iteration and the group
+// takes the argmin with shuffles (lowest k on ties, as in the plain form); the validity
+// queries of the path (one point-in-face per bounce, one occlusion test per segment) are
+// spread over the lanes the same way.  When a path is finished (iteration cap, target
+// reached, or all sub-rays invalid) the group takes the next path index from the device
+// queue head with one atomic, so paths that stop early free their group at once.
+template <int G>
+__device__ __forceinline__ void group_argmin(float &e, int &k, unsigned gmask) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        float e2 = __shfl_xor_sync(gmask, e, off, G);
+        int k2 = __shfl_xor_sync(gmask, k, off, G);
+        if (e2 < e || (e2 == e && k2 < k)) {
+            e = e2;
+            k = k2;
         }
     }
 }
 
-void refine_kernel_attrs(int *regs, int block, int *blocks_per_sm, bool batched) {
+template <int G>
+__device__ __forceinline__ void group_argmin64(double &e, int &k, unsigned gmask) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        double e2 = __shfl_xor_sync(gmask, e, off, G);
+        int k2 = __shfl_xor_sync(gmask, k, off, G);
+        if (e2 < e || (e2 == e && k2 < k)) {
+            e = e2;
+            k = k2;
+        }
+    }
+}
+
+template <int G>
+__device__ __forceinline__ int group_iterate32(const SceneDev &S, const PathGeo &g, int K, int off, double R,
+                                               dvec3 &c, double &err, int gl, unsigned gmask) {
+    float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
+    float3 u, v;
+    frame32(cf, u, v);
+    float best = INFINITY;
+    int bk = 0x7fffffff;
+    const float Rf = (float)R;
+    for (int k = gl; k < K; k += G) {
+        float sa, ca;
+        sincosf(c_sub.rho[off + k] * Rf, &sa, &ca);
+        float3 dk = cf * ca + (u * c_sub.cphi[off + k] + v * c_sub.sphi[off + k]) * sa;
+        float e = eval32(S, g, dk);
+        if (e < best) {
+            best = e;
+            bk = k;
+        }
+    }
+    group_argmin<G>(best, bk, gmask);
+    if (!(best < INFINITY)) return -1;
+    // every lane rebuilds the winning direction (same arithmetic as the lane that found it)
+    float sa, ca;
+    sincosf(c_sub.rho[off + bk] * Rf, &sa, &ca);
+    float3 bd = cf * ca + (u * c_sub.cphi[off + bk] + v * c_sub.sphi[off + bk]) * sa;
+    float inv = 1.0f / sqrtf(dot(bd, bd));
+    c = dv(bd.x * inv, bd.y * inv, bd.z * inv);
+    err = best;
+    return bk;
+}
+
+template <int G>
+__device__ __forceinline__ int group_iterate64(const SceneDev &S, const PathGeo &g, int K, int off, double R,
+                                               dvec3 &c, double &err, int gl, unsigned gmask) {
+    dvec3 u, v;
+    frame64(c, u, v);
+    double best = INFINITY;
+    int bk = 0x7fffffff;
+    for (int k = gl; k < K; k += G) {
+        double sa, ca;
+        sincos(c_sub.rho_d[off + k] * R, &sa, &ca);
+        dvec3 dk = c * ca + (u * c_sub.cphi_d[off + k] + v * c_sub.sphi_d[off + k]) * sa;
+        double e = eval64(S, g, dk);
+        if (e < best) {
+            best = e;
+            bk = k;
+        }
+    }
+    group_argmin64<G>(best, bk, gmask);
+    if (!(best < INFINITY)) return -1;
+    double sa, ca;
+    sincos(c_sub.rho_d[off + bk] * R, &sa, &ca);
+    dvec3 bd = c * ca + (u * c_sub.cphi_d[off + bk] + v * c_sub.sphi_d[off + bk]) * sa;
+    c = bd * (1.0 / dnorm(bd));
+    err = best;
+    return bk;
+}
+
+// Validity and outputs with the per-bounce / per-segment queries spread over the group.
+template <int G>
+__device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, sbr_path_record &p, int gl,
+                               unsigned gmask, double err_bound) {
+    const SceneDev &S = A.scene;
+    dvec3 pts[kMaxOrder];
+    dvec3 o = g.txd, d = c;
+    bool ok = true;
+    double gain_db = 0.0;
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j) {
+        if (j >= g.k) break;
+        Plane64 pl = S.planes_d[g.faces[j]];
+        dvec3 n = dv(pl.x, pl.y, pl.z);
+        double den = ddot(n, d);
+        double t = den != 0.0 ? (pl.w - ddot(n, o)) / den : -1.0;
+        if (!(t > 0.0)) {
+            ok = false;
+            break;
+        }
+        o = o + d * t;
+        pts[j] = o;
+        gain_db += 20.0 * log10(fresnel_perp_abs(fabs(den), (double)__ldg(S.face_eps + g.faces[j])));
+        d = d - n * (2.0 * den);
+    }
+    if (!ok) {
+        p.valid = 0;
+        p.flags |= SBR_PATH_TRACE_FAIL;
+        p.delay = 0.0;
+        return;
+    }
+    // Rx must be received on the last leg (its foot lies ahead of the last bounce point)
+    // and the refinement must have converged
+    bool mine_ok = ddot(g.rxd - o, d) > 0.0 && p.err <= err_bound;
+    for (int j = gl; j < g.k && mine_ok; j += G) mine_ok = point_in_face(S, g.faces[j], pts[j]);
+    bool valid = __all_sync(gmask, mine_ok);
+    mine_ok = true;
+    if (valid) {
+        for (int j = gl; j <= g.k && mine_ok; j += G) {
+            dvec3 from = j == 0 ? g.txd : pts[j - 1];
+            dvec3 to = j == g.k ? g.rxd : pts[j];
+            dvec3 seg = to - from;
+            int fa = j == 0 ? -1 : g.faces[j - 1];
+            int fb = j == g.k ? -1 : g.faces[j];
+            RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
+                                make_float3((float)seg.x, (float)seg.y, (float)seg.z));
+            if (any_hit(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) mine_ok = false;
+        }
+        valid = __all_sync(gmask, mine_ok);
+    }
+    double len = 0.0;
+    for (int j = 0; j <= g.k; ++j) {
+        dvec3 from = j == 0 ? g.txd : pts[j - 1];
+        dvec3 to = j == g.k ? g.rxd : pts[j];
+        len += dnorm(to - from);
+    }
+    p.valid = valid ? 1 : 0;
+    p.delay = len / kC0;
+    az_el(c, p.aod);
+    az_el((g.k > 0 ? pts[g.k - 1] : g.txd) - g.rxd, p.aoa);
+    double lam = kC0 / A.freq;
+    p.power_dbm = (float)(A.ptx_dbm + 20.0 * log10(lam / (4.0 * 3.14159265358979323846 * len)) + gain_db);
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
+    const long long total = path_count(A);
+    const int off = c_sub.off[A.K];
+    const double shrink = c_sub.shrink[A.K];
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
+    for (;;) {
+        unsigned long long q = 0;
+        if (gl == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kBatchHead), 1ULL);
+        q = __shfl_sync(gmask, q, 0, G);
+        if ((long long)q >= total) break;
+        const long long pi = (long long)q;
+        sbr_path_record p = A.paths[pi];
+        if (!path_ids_ok(A, p)) {
+            if (gl == 0) {
+                A.paths[pi].valid = 0;
+                A.paths[pi].flags = SBR_PATH_TRACE_FAIL;
+            }
+            continue;
+        }
+        PathGeo g;
+        load_path(A, p, g);
+        dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
+        double R = fmax((double)A.theta_launch, (double)p.rough_err);
+        double err = R < A.fp64_below ? eval64(A.scene, g, c)
+                                      : (double)eval32(A.scene, g, make_float3((float)c.x, (float)c.y, (float)c.z));
+        int it = 0, flags = 0;
+        while (it < A.max_iters && !(A.target > 0.0 && err <= A.target)) {
+            int bk;
+            if (R < A.fp64_below) {
+                bk = group_iterate64<G>(A.scene, g, A.K, off, R, c, err, gl, gmask);
+                flags |= SBR_PATH_FP64;
+            } else {
+                bk = group_iterate32<G>(A.scene, g, A.K, off, R, c, err, gl, gmask);
+            }
+            if (bk < 0) {
+                flags |= SBR_PATH_TRACE_FAIL;
+                break;
+            }
+            if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+            R *= shrink;
+            ++it;
+        }
+        p.iters = it;
+        p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
+        p.dir[0] = c.x;
+        p.dir[1] = c.y;
+        p.dir[2] = c.z;
+        p.err = err;
+        group_finalize<G>(A, g, c, p, gl, gmask, converged_bound(it, R));
+        if (gl == 0) store_result(A.paths + pi, p);
+    }
+}
+
+static const void *batch_fn(int lanes) {
+    switch (lanes) {
+        case 8: return (const void *)batch_refine_kernel<8>;
+        case 32: return (const void *)batch_refine_kernel<32>;
+        default: return (const void *)batch_refine_kernel<16>;
+    }
+}
+
+void refine_kernel_attrs(int *regs, int block, int *blocks_per_sm, bool batched, int lanes) {
+    const void *fn = batched ? batch_fn(lanes) : (const void *)refine_kernel;
     cudaFuncAttributes at;
-    cudaFuncGetAttributes(&at, batched ? (const void *)batch_refine_kernel : (const void *)refine_kernel);
+    cudaFuncGetAttributes(&at, fn);
     if (regs) *regs = at.numRegs;
     if (blocks_per_sm) {
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, batched ? (const void *)batch_refine_kernel : (const void *)refine_kernel, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
         *blocks_per_sm = nb > 0 ? nb : 1;
     }
 }
@@ -485,7 +627,11 @@ cudaError_t launch_refine(const RefineArgs &a, int grid, int block, cudaStream_t
 cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.counters + kBatchHead, 0, sizeof(long long), s);
     if (e != cudaSuccess) return e;
-    batch_refine_kernel<<<grid, block, 0, s>>>(a);
+    switch (a.chunk) {
+        case 8: batch_refine_kernel<8><<<grid, block, 0, s>>>(a); break;
+        case 32: batch_refine_kernel<32><<<grid, block, 0, s>>>(a); break;
+        default: batch_refine_kernel<16><<<grid, block, 0, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 

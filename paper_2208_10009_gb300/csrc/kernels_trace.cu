@@ -169,7 +169,7 @@ __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, c
 // Persistent trace kernel.  Each warp keeps 32 rays in registers; after every segment the
 // lanes whose ray ended (miss or order cap) take fresh ray ids from a global counter with
 // one warp-aggregated atomic (ballot + popc), so warps stay full until the pool drains.
-__global__ void __launch_bounds__(128) trace_kernel(TraceArgs a) {
+__global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     extern __shared__ int faces_sh_all[];                // [kMaxOrder][blockDim.x]
     int *faces_sh = faces_sh_all + threadIdx.x;
     const int stride_sh = blockDim.x;

@@ -218,12 +218,12 @@ struct RefineArgs {
     double freq;
     double ptx_dbm;
     int8_t *choice_log;
-    int chunk;
+    int chunk;                // lanes per path in the batched kernel (8, 16, 32)
     int ntx, nrx, nf;         // bounds of the ids a path record may hold
 };
 cudaError_t launch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s);
-void refine_kernel_attrs(int *regs, int block, int *blocks_per_sm, bool batched);
+void refine_kernel_attrs(int *regs, int block, int *blocks_per_sm, bool batched, int lanes);
 cudaError_t upload_subray_table(cudaStream_t s);
 
 struct PairArgs {

@@ -248,7 +248,9 @@ def large_city(seed=SEED_BASE + 5, blocks=60, pitch=55.0, terrain_cells=700, ntx
         for bj in range(blocks):
             k = int(rng.integers(6, 13))
             r = rng.uniform(10.0, 18.0)
-            ang = np.sort(rng.uniform(0, 2 * np.pi, k))
+            # evenly spaced corners jittered by up to a third of the spacing: convex, no
+            # degenerate edges
+            ang = (np.arange(k) + rng.uniform(-1 / 3, 1 / 3, k)) * (2 * np.pi / k) + rng.uniform(0, 2 * np.pi)
             cx, cy = bi * pitch + pitch / 2, bj * pitch + pitch / 2
             px, py = cx + r * np.cos(ang), cy + r * np.sin(ang)
             base = float(height(px, py).min()) - 3.0

@@ -79,7 +79,10 @@ def _refine_compare(gpu_ctx, oracle_mod, S, tx, rx, got, n, K, iters, alpha, tar
                 near_ties += 1
                 continue
         assert ang(r["dir"], ref["dir"]) < TOL_ANGLE_RAD, (faces, ang(r["dir"], ref["dir"]))
-        ev = oracle_mod.path_eval(S, tx[r["tx"]], rx[r["rx"]], faces, ref["dir"])
+        # outputs evaluated on the GPU's own refined direction
+        R0 = max(tl, float(r["rough_err"]))
+        bound = oracle_mod.refined_err_bound(R0, K, int(r["iters"])) if r["iters"] > 0 else 0.0
+        ev = oracle_mod.path_eval(S, tx[r["tx"]], rx[r["rx"]], faces, r["dir"], err_bound=bound)
         assert bool(r["valid"]) == ev["valid"], faces
         assert abs(r["delay"] / ev["delay"] - 1) < TOL_DELAY_REL
         assert ang(dir_of(*r["aod"]), dir_of(*ev["aod"])) < TOL_ANGLE_RAD
@@ -212,12 +215,13 @@ def test_batched_and_per_pair_equal_plain(gpu_ctx):
     sc, tx, rx = scenes.office(nbox=60, ntx=2, nrx=12, g_shell=8, g_box=1)
     scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx, 1 << 18, 1 << 16)
     res = []
-    for mode in ("plain", "batch", "pair"):
+    for mode in ("plain", "batch", "batch8", "batch32", "pair"):
         gpu_ctx.launch(scene, tx, rxs, paths, 48, 3, rx_angle_scale=SQ3, sync=True)
         if mode == "plain":
             gpu_ctx.refine(scene, paths, 8, 16, target=np.radians(0.01))
-        elif mode == "batch":
-            gpu_ctx.batch_refine(scene, paths, 8, 16, target=np.radians(0.01), chunk=2)
+        elif mode.startswith("batch"):
+            lanes = int(mode[5:] or 16)
+            gpu_ctx.batch_refine(scene, paths, 8, 16, target=np.radians(0.01), lanes_per_path=lanes)
         else:
             for t in range(len(tx)):
                 for r in range(len(rx)):
