@@ -31,9 +31,10 @@ WORKLOAD = dict(workload="urban canyon: 20x20 box city + ground (~10k tris), 1 T
                          "alpha=sqrt(3), 6 refinement iterations, K=9",
                 n_div=700, max_order=6, alpha=float(np.sqrt(3.0)), iters=6, K=9)
 ACC_DEG = 0.01
-# FLOPs per unit of the trace kernel (counted from the kernel source): slab test of a node's
-# two child boxes, one watertight triangle test, one receiver candidate test
-FLOP_NODE, FLOP_TRI, FLOP_RX = 24, 40, 20
+# FLOPs per unit of the trace kernel (counted from the kernel source): a 4-wide node visit
+# (four child slab tests of 6 FMA each), one watertight triangle test, one receiver
+# candidate test
+FLOP_NODE, FLOP_TRI, FLOP_RX = 48, 40, 20
 L2_FLUSH_BYTES = 256 << 20
 
 

@@ -147,7 +147,7 @@ typedef struct {
 typedef struct {
     int64_t rays;            /* rays traced (ntx * N) */
     int64_t segments;        /* closest-hit queries = ray-bounces */
-    int64_t node_visits;     /* BVH inner nodes visited */
+    int64_t node_visits;     /* 4-wide BVH nodes visited by the trace (four box tests each) */
     int64_t tri_tests;       /* ray-triangle tests */
     int64_t rx_tests;        /* candidate Rx tested */
     int64_t records;         /* reception records emitted (may exceed record_cap) */

@@ -309,6 +309,9 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     BvhOut bvh;
     std::string err;
     if (!build_bvh(blo, bhi, kLeafMax, bvh, err)) return fail(ctx, SBR_EDEGENERATE, err);
+    if (bvh.max_stack4 > kStack4)
+        return fail(ctx, SBR_EDEGENERATE, "scene: BVH too deep for the traversal stack (" +
+                                              std::to_string(bvh.max_stack4) + " entries)");
     // triangles in BVH order, face CSR
     std::vector<float4> tri4(3 * (size_t)nt);
     std::vector<int> off((size_t)nf + 1, 0), idx((size_t)nt);
@@ -334,12 +337,13 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     }
     sbr_scene *sc = new (std::nothrow) sbr_scene();
     if (!sc) return fail(ctx, SBR_ENOMEM, "scene: host allocation failed");
-    float4 *d_nodes, *d_tris, *d_pl;
+    float4 *d_nodes, *d_nodes4, *d_tris, *d_pl;
     Plane64 *d_pld;
     float *d_eps;
     int *d_off, *d_idx;
     Carver cv;
     cv.add(&d_nodes, bvh.nodes.size());
+    cv.add(&d_nodes4, bvh.nodes4.size());
     cv.add(&d_tris, tri4.size());
     cv.add(&d_pl, pl4.size());
     cv.add(&d_pld, planes.size());
@@ -355,6 +359,7 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     cv.bind(sc->mem);
     cudaStream_t s = ctx->stream;
     SBR_CUDA(cudaMemcpyAsync(d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+    SBR_CUDA(cudaMemcpyAsync(d_nodes4, bvh.nodes4.data(), bvh.nodes4.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     if (nt) SBR_CUDA(cudaMemcpyAsync(d_tris, tri4.data(), tri4.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_pl, pl4.data(), pl4.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_pld, planes.data(), planes.size() * sizeof(Plane64), cudaMemcpyHostToDevice, s));
@@ -363,6 +368,7 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     if (nt) SBR_CUDA(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaStreamSynchronize(s));
     sc->dev.nodes = d_nodes;
+    sc->dev.nodes4 = d_nodes4;
     sc->dev.tris = d_tris;
     sc->dev.planes = d_pl;
     sc->dev.planes_d = d_pld;
@@ -421,6 +427,7 @@ sbr_status sbr_rx_upload(sbr_ctx *ctx, const float *rx, int32_t nrx, sbr_rxset *
     BvhOut bvh;
     std::string err;
     if (!build_bvh(host, host, 4, bvh, err)) return fail(ctx, SBR_EINVAL, err);
+    if (bvh.max_stack4 > kStack4) return fail(ctx, SBR_EINVAL, "sbr_rx_upload: receiver BVH too deep");
     std::vector<float4> pts((size_t)std::max(nrx, 1)), by_id((size_t)std::max(nrx, 1));
     sbr_rxset *rs = new (std::nothrow) sbr_rxset();
     if (!rs) return fail(ctx, SBR_ENOMEM, "rx: host allocation failed");
@@ -437,9 +444,10 @@ sbr_status sbr_rx_upload(sbr_ctx *ctx, const float *rx, int32_t nrx, sbr_rxset *
             rs->dev.hi[a] = std::max(rs->dev.hi[a], host[3 * i + a]);
         }
     }
-    float4 *d_nodes, *d_pts, *d_by;
+    float4 *d_nodes, *d_nodes4, *d_pts, *d_by;
     Carver cv;
     cv.add(&d_nodes, bvh.nodes.size());
+    cv.add(&d_nodes4, bvh.nodes4.size());
     cv.add(&d_pts, pts.size());
     cv.add(&d_by, by_id.size());
     rs->mem = dev_alloc(ctx, cv.total);
@@ -451,10 +459,13 @@ sbr_status sbr_rx_upload(sbr_ctx *ctx, const float *rx, int32_t nrx, sbr_rxset *
     cv.bind(rs->mem);
     SBR_CUDA(cudaMemcpyAsync(d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(float4), cudaMemcpyHostToDevice,
                              ctx->stream));
+    SBR_CUDA(cudaMemcpyAsync(d_nodes4, bvh.nodes4.data(), bvh.nodes4.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                             ctx->stream));
     SBR_CUDA(cudaMemcpyAsync(d_pts, pts.data(), pts.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
     SBR_CUDA(cudaMemcpyAsync(d_by, by_id.data(), by_id.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
     SBR_CUDA(cudaStreamSynchronize(ctx->stream));
     rs->dev.nodes = d_nodes;
+    rs->dev.nodes4 = d_nodes4;
     rs->dev.pts = d_pts;
     rs->dev.by_id = d_by;
     rs->dev.nrx = nrx;

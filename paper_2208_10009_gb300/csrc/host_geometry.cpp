@@ -2,6 +2,7 @@
 // equiangular lattice's layer tables (§II.B, Eq. 1-2) and the precise algorithm's
 // sub-ray patterns (§III.B, Fig. 5).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -207,6 +208,98 @@ bool build_bvh(const std::vector<float> &lo, const std::vector<float> &hi, int l
     if (b.max_leaf > 127) {
         err = "BVH: leaf larger than 127 primitives (degenerate input)";
         return false;
+    }
+    // 4-wide collapse: a node adopts the children of its largest inner children until it
+    // has four (or none of its children is inner).
+    {
+        std::vector<std::array<int, 4>> kids;
+        std::vector<int> nkids;
+        std::vector<int> wide_of(b.nodes.size(), -1);
+        auto collapse = [&](int id) {
+            std::array<int, 4> c = {-1, -1, -1, -1};
+            int n = 0;
+            const TmpNode &t = b.nodes[id];
+            if (t.left < 0) {
+                c[n++] = id;   // a leaf root
+            } else {
+                c[n++] = t.left;
+                c[n++] = t.right;
+                while (n < 4) {
+                    int best = -1;
+                    float area = -1.0f;
+                    for (int i = 0; i < n; ++i) {
+                        const TmpNode &ch = b.nodes[c[i]];
+                        if (ch.left >= 0 && ch.box.area() > area) {
+                            area = ch.box.area();
+                            best = i;
+                        }
+                    }
+                    if (best < 0) break;
+                    int inner = c[best];
+                    c[best] = b.nodes[inner].left;
+                    c[n++] = b.nodes[inner].right;
+                }
+            }
+            return std::make_pair(c, n);
+        };
+        std::vector<int> order4, st4;
+        if (!b.nodes.empty()) st4.push_back(0);
+        while (!st4.empty()) {
+            int id = st4.back();
+            st4.pop_back();
+            wide_of[id] = (int)order4.size();
+            order4.push_back(id);
+            auto cn = collapse(id);
+            kids.push_back(cn.first);
+            nkids.push_back(cn.second);
+            for (int i = cn.second - 1; i >= 0; --i)
+                if (b.nodes[cn.first[i]].left >= 0 && cn.first[i] != id) st4.push_back(cn.first[i]);
+        }
+        out.nodes4.assign(order4.size() > 0 ? order4.size() * 8 : 8, make_float4(0, 0, 0, 0));
+        auto put4 = [&](float4 *nd, int slot, const Box &bx) {
+            float *f = reinterpret_cast<float *>(nd);
+            bool empty = !(bx.hi[0] >= bx.lo[0]);
+            for (int a = 0; a < 3; ++a) {
+                f[(2 * a) * 4 + slot] = empty ? 1e30f : bx.lo[a];
+                f[(2 * a + 1) * 4 + slot] = empty ? 1e30f : bx.hi[a];
+            }
+        };
+        if (order4.empty()) {
+            Box empty;
+            for (int i = 0; i < 4; ++i) put4(&out.nodes4[0], i, empty);
+            int *ref = reinterpret_cast<int *>(&out.nodes4[6]);
+            for (int i = 0; i < 4; ++i) ref[i] = leaf_ref(0, 0);
+        }
+        // worst-case stack: along a root-to-leaf path every node pushes up to nkids - 1
+        // siblings that stay on the stack while its subtree is traversed
+        {
+            std::vector<int> need(order4.size(), 0);
+            for (size_t w = order4.size(); w-- > 0;) {
+                int deepest = 0;
+                for (int i = 0; i < nkids[w]; ++i) {
+                    int c = kids[w][i];
+                    if (b.nodes[c].left >= 0 && c != order4[w]) deepest = std::max(deepest, need[wide_of[c]]);
+                }
+                need[w] = nkids[w] - 1 + deepest;
+            }
+            out.max_stack4 = need.empty() ? 0 : need[0];
+        }
+        for (size_t w = 0; w < order4.size(); ++w) {
+            float4 *nd = &out.nodes4[8 * w];
+            int *ref = reinterpret_cast<int *>(&nd[6]);
+            Box empty;
+            for (int i = 0; i < 4; ++i) {
+                int c = i < nkids[w] ? kids[w][i] : -1;
+                if (c < 0) {
+                    put4(nd, i, empty);
+                    ref[i] = leaf_ref(0, 0);
+                    continue;
+                }
+                const TmpNode &t = b.nodes[c];
+                put4(nd, i, t.box);
+                ref[i] = (t.left >= 0 && c != order4[w]) ? wide_of[c] : leaf_ref(t.first, t.count);
+            }
+        }
     }
     out.prim_order = b.idx;
     out.depth = b.depth;

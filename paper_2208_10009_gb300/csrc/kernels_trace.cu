@@ -74,24 +74,6 @@ cudaError_t launch_raygen(const LatticeDev &lat, float4 *dirs, int64_t N, cudaSt
 }
 
 // ----------------------------------------------------------------------------- a2-a4
-__device__ __forceinline__ int slab2_expand(const float4 *node, const RayPre &r, float tmax, float rad, float &e0,
-                                            float &e1) {
-    float4 a = __ldg(node + 0), b = __ldg(node + 1), c = __ldg(node + 2);
-    float lx0 = (a.x - rad - r.o.x) * r.inv.x, hx0 = (a.w + rad - r.o.x) * r.inv.x;
-    float ly0 = (a.y - rad - r.o.y) * r.inv.y, hy0 = (b.x + rad - r.o.y) * r.inv.y;
-    float lz0 = (a.z - rad - r.o.z) * r.inv.z, hz0 = (b.y + rad - r.o.z) * r.inv.z;
-    float lx1 = (b.z - rad - r.o.x) * r.inv.x, hx1 = (c.y + rad - r.o.x) * r.inv.x;
-    float ly1 = (b.w - rad - r.o.y) * r.inv.y, hy1 = (c.z + rad - r.o.y) * r.inv.y;
-    float lz1 = (c.x - rad - r.o.z) * r.inv.z, hz1 = (c.w + rad - r.o.z) * r.inv.z;
-    float n0 = fmaxf(fmaxf(fminf(lx0, hx0), fminf(ly0, hy0)), fmaxf(fminf(lz0, hz0), 0.0f));
-    float f0 = fminf(fminf(fmaxf(lx0, hx0), fmaxf(ly0, hy0)), fminf(fmaxf(lz0, hz0), tmax)) * 1.0000005f;
-    float n1 = fmaxf(fmaxf(fminf(lx1, hx1), fminf(ly1, hy1)), fmaxf(fminf(lz1, hz1), 0.0f));
-    float f1 = fminf(fminf(fmaxf(lx1, hx1), fmaxf(ly1, hy1)), fminf(fmaxf(lz1, hz1), tmax)) * 1.0000005f;
-    e0 = n0;
-    e1 = n1;
-    return (n0 <= f0 ? 1 : 0) | (n1 <= f1 ? 2 : 0);
-}
-
 struct LaneRay {
     float3 o, d;
     float L;
@@ -100,7 +82,10 @@ struct LaneRay {
 
 // Reception judgment on segment o + s d, s in [0, tseg], of a ray that has travelled L
 // metres before it: every Rx whose foot lies on the segment and whose error angle
-// (Eq. 3) is within the cone emits a record.
+// (Eq. 3) is within the cone emits a record.  Candidates come from the receivers' 4-wide
+// BVH, each box grown by the cone radius at the segment's far end; the growth is folded
+// into the per-segment slab offsets (near: o/d + rad/|d|, far: o/d - rad/|d|), so a grown
+// box costs what a plain one does.
 __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, const LaneRay &st, float tseg,
                                           const int *faces_sh, int stride_sh, unsigned &rx_tests) {
     const RxDev &R = a.rx;
@@ -108,24 +93,43 @@ __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, c
     float tcap = fminf(tseg, max_foot(R, st.o, st.d));
     if (!(tcap >= 0.0f)) return;
     float rad = (st.L + tcap) * a.tan_cone * 1.001f + 1e-5f;
-    int stack[kStackDepth];
+    const float oix = r.o.x * r.inv.x, oiy = r.o.y * r.inv.y, oiz = r.o.z * r.inv.z;
+    const float gx = rad * fabsf(r.inv.x), gy = rad * fabsf(r.inv.y), gz = rad * fabsf(r.inv.z);
+    const float cnx = oix + gx, cny = oiy + gy, cnz = oiz + gz;
+    const float cfx = oix - gx, cfy = oiy - gy, cfz = oiz - gz;
+    const float tfar = tcap * 1.0000005f + 1e-6f;
+    int stack[kStack4];
     int sp = 0;
     int node = 0;
     for (;;) {
         if (!is_leaf(node)) {
-            const float4 *nd = R.nodes + 4 * (size_t)node;
-            float e0, e1;
-            int m = slab2_expand(nd, r, tcap, rad, e0, e1);
-            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 3));
-            if (m == 3) {
-                stack[sp++] = refs.y;
-                node = refs.x;
-                continue;
-            } else if (m == 1) {
-                node = refs.x;
-                continue;
-            } else if (m == 2) {
-                node = refs.y;
+            const float4 *nd = R.nodes4 + 8 * (size_t)node;
+            float4 nxv = __ldg(nd + r.nx), fxv = __ldg(nd + 1 - r.nx);
+            float4 nyv = __ldg(nd + 2 + r.ny), fyv = __ldg(nd + 3 - r.ny);
+            float4 nzv = __ldg(nd + 4 + r.nz), fzv = __ldg(nd + 5 - r.nz);
+            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 6));
+            const float2 nx01 = fma2s(nxv.x, nxv.y, r.inv.x, -cnx), nx23 = fma2s(nxv.z, nxv.w, r.inv.x, -cnx);
+            const float2 fx01 = fma2s(fxv.x, fxv.y, r.inv.x, -cfx), fx23 = fma2s(fxv.z, fxv.w, r.inv.x, -cfx);
+            const float2 ny01 = fma2s(nyv.x, nyv.y, r.inv.y, -cny), ny23 = fma2s(nyv.z, nyv.w, r.inv.y, -cny);
+            const float2 fy01 = fma2s(fyv.x, fyv.y, r.inv.y, -cfy), fy23 = fma2s(fyv.z, fyv.w, r.inv.y, -cfy);
+            const float2 nz01 = fma2s(nzv.x, nzv.y, r.inv.z, -cnz), nz23 = fma2s(nzv.z, nzv.w, r.inv.z, -cnz);
+            const float2 fz01 = fma2s(fzv.x, fzv.y, r.inv.z, -cfz), fz23 = fma2s(fzv.z, fzv.w, r.inv.z, -cfz);
+            const float tnx[4] = {nx01.x, nx01.y, nx23.x, nx23.y}, tfx[4] = {fx01.x, fx01.y, fx23.x, fx23.y};
+            const float tny[4] = {ny01.x, ny01.y, ny23.x, ny23.y}, tfy[4] = {fy01.x, fy01.y, fy23.x, fy23.y};
+            const float tnz[4] = {nz01.x, nz01.y, nz23.x, nz23.y}, tfz[4] = {fz01.x, fz01.y, fz23.x, fz23.y};
+            const int rf[4] = {refs.x, refs.y, refs.z, refs.w};
+            int next = 0x7fffffff;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float tn = max3f(tnx[c], tny[c], fmaxf(tnz[c], 0.0f));
+                float tf = min3f(tfx[c], tfy[c], fminf(tfz[c], tfar)) * 1.0000005f;
+                if (tn <= tf) {
+                    if (next == 0x7fffffff) next = rf[c];
+                    else stack[sp++] = rf[c];
+                }
+            }
+            if (next != 0x7fffffff) {
+                node = next;
                 continue;
             }
         } else {
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         RayPre r = make_ray(st.o, st.d);
         float th;
         int face;
-        int hit = closest_hit(a.scene, r, a.scene.tmin, INFINITY, st.prev, th, face, nodes, tris);
+        int hit = closest_hit4(a.scene, r, a.scene.tmin, INFINITY, st.prev, th, face, nodes, tris);
         ++seg;
         if (a.dump_stride > 0 && st.ray % a.dump_stride == 0)
             a.dump_faces[((size_t)st.txi * a.dump_per_tx + st.ray / a.dump_stride) * (a.max_order + 1) + st.k] =

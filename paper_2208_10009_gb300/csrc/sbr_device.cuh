@@ -37,14 +37,21 @@ struct RayPre {
     float3 o, d, inv;
     int kx, ky, kz;
     float Sx, Sy, Sz;
+    int nx, ny, nz;   // 1 where 1/d < 0: the near slab plane is the box's hi side
 };
 
 __device__ __forceinline__ RayPre make_ray(float3 o, float3 d) {
     RayPre r;
     r.o = o;
     r.d = d;
-    // 1/0 -> +-inf keeps the slab test correct for axis-parallel rays
-    r.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    // A zero component is replaced by 1e-30 before inverting: the slab tests stay correct
+    // for axis-parallel rays (huge but finite t), and box * inv - o * inv never forms
+    // inf - inf.
+    r.inv = make_float3(1.0f / (d.x != 0.0f ? d.x : 1e-30f), 1.0f / (d.y != 0.0f ? d.y : 1e-30f),
+                        1.0f / (d.z != 0.0f ? d.z : 1e-30f));
+    r.nx = r.inv.x < 0.0f;
+    r.ny = r.inv.y < 0.0f;
+    r.nz = r.inv.z < 0.0f;
     float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
     int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
     int kx = kz == 2 ? 0 : kz + 1;
@@ -139,6 +146,121 @@ __device__ __forceinline__ int closest_hit(const SceneDev &S, const RayPre &r, f
                 continue;
             } else if (m == 2) {
                 node = refs.y;
+                continue;
+            }
+        } else {
+            int first = leaf_first(node), cnt = leaf_count(node);
+            for (int i = first; i < first + cnt; ++i) {
+                const float4 *t = S.tris + 3 * (size_t)i;
+                float4 a = __ldg(t), b = __ldg(t + 1), c = __ldg(t + 2);
+                int f = __float_as_int(a.w);
+                if (f == skip) continue;
+                ++tris_tested;
+                float th = tri_watertight(r, a, b, c);
+                if (!(th > tmin) || th > tbest) continue;
+                if (th < tbest || f < bface || (f == bface && i < best)) {
+                    tbest = th;
+                    best = i;
+                    bface = f;
+                }
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    t_out = tbest;
+    face_out = bface;
+    return best;
+}
+
+// Three-input min / max (one instruction each on sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+// Two FMAs in one packed f32x2 instruction: (a.x * b + c, a.y * b + c).
+__device__ __forceinline__ float2 fma2s(float ax, float ay, float b, float c) {
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %4};\n\t"
+        "mov.b64 pc, {%5, %5};\n\t"
+        "fma.rn.f32x2 pd, pa, pb, pc;\n\t"
+        "mov.b64 {%0, %1}, pd;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(ax), "f"(ay), "f"(b), "f"(c));
+    return r;
+}
+
+// Compare-exchange of (distance, ref) pairs: smaller distance first.
+__device__ __forceinline__ void cswap(float &da, int &ra, float &db, int &rb) {
+    bool sw = db < da;
+    float d = sw ? db : da;
+    int r = sw ? rb : ra;
+    db = sw ? da : db;
+    rb = sw ? ra : rb;
+    da = d;
+    ra = r;
+}
+
+// Closest hit through the 4-wide BVH.  Per node, slab tests of the four child boxes as
+// t = plane * (1/d) - o * (1/d), the near / far planes picked by the ray's direction
+// signs (so no per-axis min/max), two children per packed FMA and three-input min/max;
+// the hit children are sorted by entry distance, the nearest is visited next and the
+// others pushed farthest first.  Same hit rule as closest_hit.  nodes_visited counts
+// 4-wide nodes (four box tests each).
+__device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, float tmin, float tmax, int skip,
+                                            float &t_out, int &face_out, unsigned &nodes_visited,
+                                            unsigned &tris_tested) {
+    int stack[kStack4];
+    int sp = 0;
+    int node = 0;
+    float tbest = tmax;
+    int best = -1, bface = 0x7fffffff;
+    const float oix = r.o.x * r.inv.x, oiy = r.o.y * r.inv.y, oiz = r.o.z * r.inv.z;
+    for (;;) {
+        if (!is_leaf(node)) {
+            ++nodes_visited;
+            const float4 *nd = S.nodes4 + 8 * (size_t)node;
+            float4 nxv = __ldg(nd + r.nx), fxv = __ldg(nd + 1 - r.nx);
+            float4 nyv = __ldg(nd + 2 + r.ny), fyv = __ldg(nd + 3 - r.ny);
+            float4 nzv = __ldg(nd + 4 + r.nz), fzv = __ldg(nd + 5 - r.nz);
+            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 6));
+            const float2 nx01 = fma2s(nxv.x, nxv.y, r.inv.x, -oix), nx23 = fma2s(nxv.z, nxv.w, r.inv.x, -oix);
+            const float2 fx01 = fma2s(fxv.x, fxv.y, r.inv.x, -oix), fx23 = fma2s(fxv.z, fxv.w, r.inv.x, -oix);
+            const float2 ny01 = fma2s(nyv.x, nyv.y, r.inv.y, -oiy), ny23 = fma2s(nyv.z, nyv.w, r.inv.y, -oiy);
+            const float2 fy01 = fma2s(fyv.x, fyv.y, r.inv.y, -oiy), fy23 = fma2s(fyv.z, fyv.w, r.inv.y, -oiy);
+            const float2 nz01 = fma2s(nzv.x, nzv.y, r.inv.z, -oiz), nz23 = fma2s(nzv.z, nzv.w, r.inv.z, -oiz);
+            const float2 fz01 = fma2s(fzv.x, fzv.y, r.inv.z, -oiz), fz23 = fma2s(fzv.z, fzv.w, r.inv.z, -oiz);
+            const float tnx[4] = {nx01.x, nx01.y, nx23.x, nx23.y}, tfx[4] = {fx01.x, fx01.y, fx23.x, fx23.y};
+            const float tny[4] = {ny01.x, ny01.y, ny23.x, ny23.y}, tfy[4] = {fy01.x, fy01.y, fy23.x, fy23.y};
+            const float tnz[4] = {nz01.x, nz01.y, nz23.x, nz23.y}, tfz[4] = {fz01.x, fz01.y, fz23.x, fz23.y};
+            float dist[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float tn = max3f(tnx[c], tny[c], fmaxf(tnz[c], tmin));
+                float tf = min3f(tfx[c], tfy[c], fminf(tfz[c], tbest)) * 1.0000005f;
+                dist[c] = tn <= tf ? tn : INFINITY;
+            }
+            float d0 = dist[0], d1 = dist[1], d2 = dist[2], d3 = dist[3];
+            int r0 = refs.x, r1 = refs.y, r2 = refs.z, r3 = refs.w;
+            cswap(d0, r0, d1, r1);
+            cswap(d2, r2, d3, r3);
+            cswap(d0, r0, d2, r2);
+            cswap(d1, r1, d3, r3);
+            cswap(d1, r1, d2, r2);
+            int h = (d0 < INFINITY) + (d1 < INFINITY) + (d2 < INFINITY) + (d3 < INFINITY);
+            if (h > 0) {
+                if (h > 3) stack[sp++] = r3;
+                if (h > 2) stack[sp++] = r2;
+                if (h > 1) stack[sp++] = r1;
+                node = r0;
                 continue;
             }
         } else {

@@ -16,6 +16,7 @@ constexpr int kMaxOrder = SBR_MAX_ORDER;
 constexpr double kC0 = 299792458.0;
 constexpr int kLeafMax = 4;        // triangles per BVH leaf (target)
 constexpr int kStackDepth = 64;    // traversal stack entries (BVH depth is capped below this)
+constexpr int kStack4 = 96;        // 4-wide traversal stack (the builder checks the bound)
 
 // Device counters of one launch (int64 each).
 enum Counter {
@@ -42,7 +43,13 @@ struct __align__(32) Plane64 {
     double x, y, z, w;
 };
 
+// BVH4 node (128 bytes = 8 x float4) used by the trace kernel: the four children's boxes
+// in structure-of-arrays form, f[0] = lo.x of children 0..3, f[1] = hi.x, f[2] = lo.y,
+// f[3] = hi.y, f[4] = lo.z, f[5] = hi.z; f[6] = the four child refs (same encoding as
+// BVH2; an empty slot is a leaf with 0 primitives and a far-away point box); f[7] unused.
+
 struct SceneDev {
+    const float4 *nodes4;     // 8 per BVH4 node
     const float4 *nodes;      // 4 per node
     const float4 *tris;       // 3 per triangle: (v0, face id bits), (v1, 0), (v2, 0)
     const float4 *planes;     // per face: (n, h) with n.x = h on the plane
@@ -55,6 +62,7 @@ struct SceneDev {
 };
 
 struct RxDev {
+    const float4 *nodes4;     // 4-wide BVH over receivers (same node layout as the scene's)
     const float4 *nodes;      // BVH over receivers (same node layout)
     const float4 *pts;        // BVH order: (x, y, z, original id bits)
     const float4 *by_id;      // original order: (x, y, z, 0)
@@ -155,6 +163,8 @@ void dev_free(sbr_ctx *ctx, void *p, size_t bytes);
 // host geometry (host_geometry.cpp)
 struct BvhOut {
     std::vector<float4> nodes;
+    std::vector<float4> nodes4;    // the same tree collapsed to 4-wide nodes
+    int max_stack4 = 0;            // worst-case 4-wide traversal stack use
     std::vector<int> prim_order;   // BVH leaf order -> original primitive index
     int depth = 0, max_leaf = 0;
 };
