@@ -38,6 +38,32 @@ FLOP_NODE, FLOP_TRI, FLOP_RX = 48, 40, 20
 L2_FLUSH_BYTES = 256 << 20
 
 
+TRACE_SOURCES = ["paper_2208_10009_gb300/csrc/kernels_trace.cu", "paper_2208_10009_gb300/csrc/sbr_device.cuh",
+                 "paper_2208_10009_gb300/csrc/sbr_internal.h"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_kernel_traffic.json")
+
+
+def trace_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRACE_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def trace_traffic():
+    """DRAM bytes per trace launch from the committed ncu record, or None when the kernel
+    sources have changed since it was captured."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except Exception:
+        return None, None
+    if rec.get("source_sha256") != trace_source_hash():
+        return None, rec
+    return rec["dram_bytes_per_launch"], rec
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -47,7 +73,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms during the timed region."""
     FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
               "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
               "clocks_event_reasons.sw_power_cap"]
@@ -61,7 +87,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.file, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
         return self
@@ -240,6 +266,7 @@ def run_gpu(args):
     sms = ctx.num_sms
     peak_tflops = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = flops / (st_t["ms_trace"] / 1e3) / 1e12
+    traffic, traffic_rec = trace_traffic()
 
     # the batched graph form vs the plain per-pair launch-and-refine form
     per_pair_ms = _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, len(rx))
@@ -263,15 +290,17 @@ def run_gpu(args):
            "refine_batched_graph_ms": batch_ms, "refine_per_pair_ms": per_pair_ms,
            "batch_refine_shape": dict(shape, tuned_ms=tuned["ms"]),
            "roofline": {"bound": "alu", "kernel": "trace_kernel", "achieved": achieved, "peak": peak_tflops,
-                        "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                        "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                        "traffic_source": None if traffic is None else traffic_rec.get("capture"),
                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} MEASURED_PEAKS.json)",
                         "flops_per_launch": flops},
            "clocks": clocks, "gpu_launches": 6 * args.steps, "wall_s": t_wall, "e2e": e2e}
     if rank == 0 and not args.no_cpu_baseline:
-        s, g, dt, nr, cores = cpu_oracle_sample(sc, tx, rx, 997)
+        stride = 7
+        s, g, dt, nr, cores = cpu_oracle_sample(sc, tx, rx, stride)
         out["cpu_baseline"] = {"value": s / dt, "unit": "ray-bounces/s", "cores": cores, "kind": "oracle",
-                               "sample": f"every 997th ray id ({nr} rays): brute-force FP64 trace, dedup, refine, "
-                                         f"validity; {dt:.1f} s", "refined_paths_per_s": g / dt}
+                               "sample": f"every {stride}th ray id ({nr} rays, {s} ray-bounces): brute-force FP64 "
+                                         f"trace, dedup, refine, validity; {dt:.1f} s", "refined_paths_per_s": g / dt}
     if rank == 0:
         print(json.dumps(out), flush=True)
     for h in (paths, rxs, scene):
@@ -379,7 +408,7 @@ def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

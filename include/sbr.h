@@ -138,7 +138,9 @@ typedef struct {
                                 (-1 miss, -2 not traced), or NULL */
     int64_t dump_cap;        /* int32 entries in dump_faces; SBR_EINVAL if too small */
     int32_t grid_blocks;     /* persistent trace grid (0 = one wave over all SMs) */
-    int32_t block_threads;   /* 0 = default (128) */
+    int32_t block_threads;   /* multiple of 32, at most 128 (0 = 128) */
+    int32_t refill_min;      /* a warp takes new rays once this many of its lanes are idle
+                                (1..32; 0 = 16: keeps a warp's rays neighbours in the lattice) */
 } sbr_launch_params;
 
 #define SBR_LAUNCH_SYNC 1    /* synchronise at the end and report overflow / collisions */

@@ -37,7 +37,7 @@ class SceneInfo(_c.Structure):
 class LaunchParams(_c.Structure):
     _fields_ = [("n_div", _i32), ("max_order", _i32), ("rx_angle_scale", _f32), ("flags", _i32),
                 ("dump_stride", _i32), ("dump_faces", _vp), ("dump_cap", _i64), ("grid_blocks", _i32),
-                ("block_threads", _i32)]
+                ("block_threads", _i32), ("refill_min", _i32)]
 
 
 class LaunchStats(_c.Structure):

@@ -178,7 +178,7 @@ class Context:
     def launch(self, scene: Scene, tx, rx: RxSet, paths: Paths, n_div: int, max_order: int,
                rx_angle_scale: float = 1.0, sync: bool = False, dump_stride: int = 0,
                dump: torch.Tensor | None = None, grid_blocks: int = 0, block_threads: int = 0,
-               timing: bool = False):
+               timing: bool = False, refill_min: int = 0):
         """a1-a5: ray generation, trace with reception, double-count removal.  `tx` is an
         (ntx, 3) array on the host (numpy) or the device (torch)."""
         if isinstance(tx, torch.Tensor):
@@ -189,7 +189,8 @@ class Context:
             txp, ntx = keep.ctypes.data, len(keep)
         flags = (B.LAUNCH_SYNC if sync else 0) | (B.LAUNCH_TIMING if timing else 0)
         prm = B.LaunchParams(n_div, max_order, rx_angle_scale, flags, dump_stride,
-                             _ptr(dump), 0 if dump is None else dump.numel(), grid_blocks, block_threads)
+                             _ptr(dump), 0 if dump is None else dump.numel(), grid_blocks, block_threads,
+                             refill_min)
         self._check(self.lib.sbr_launch(self.handle, scene.handle, txp, ntx, rx.handle, ctypes.byref(prm),
                                         paths.handle))
         del keep

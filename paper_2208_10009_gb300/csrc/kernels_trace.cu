@@ -170,10 +170,12 @@ __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, c
     }
 }
 
-// Persistent trace kernel.  Each warp keeps 32 rays in registers; after every segment the
-// lanes whose ray ended (miss or order cap) take fresh ray ids from a global counter with
-// one warp-aggregated atomic (ballot + popc), so warps stay full until the pool drains.
-__global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
+// Persistent trace kernel.  Each warp keeps 32 rays in registers; after a segment, once at
+// least refill_min lanes hold a finished ray (miss or order cap), those lanes take fresh,
+// consecutive ray ids from a global counter with one warp-aggregated atomic (ballot +
+// popc).  Waiting for several idle lanes keeps a warp's rays neighbours in the lattice
+// (coherent traversal) while still keeping warps mostly full until the pool drains.
+__global__ void __launch_bounds__(128, 8) trace_kernel(TraceArgs a) {
     extern __shared__ int faces_sh_all[];                // [kMaxOrder][blockDim.x]
     int *faces_sh = faces_sh_all + threadIdx.x;
     const int stride_sh = blockDim.x;
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     st.k = st.prev = st.txi = st.ray = 0;
     for (;;) {
         unsigned need = __ballot_sync(0xffffffffu, !alive);
-        if (need && !pool_empty) {
+        if (need && !pool_empty && (__popc(need) >= a.refill_min || need == 0xffffffffu)) {
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kRayHead),
                                             (unsigned long long)__popc(need));

@@ -196,6 +196,7 @@ struct TraceArgs {
     int dump_stride;
     int *dump_faces;
     int64_t dump_per_tx;
+    int refill_min;           // a warp takes new rays once at least this many lanes are idle
 };
 cudaError_t launch_trace(const TraceArgs &a, int grid, int block, cudaStream_t s);
 
