@@ -126,6 +126,17 @@ def _dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time (every rank gets it); the time itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_oracle_sample(sc, tx, rx, stride, offset=0):
     """The oracle (as it stands) on every `stride`-th ray of the workload: trace, dedup,
     refinement, validity and outputs.  Returns (ray-bounces, refined paths, seconds)."""
@@ -245,11 +256,7 @@ def run_gpu(args):
         t_wall = time.perf_counter() - t_wall
     if world > 1:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dev)
     clocks = clk.summary()
     st = ctx.launch_stats(paths)
     recs = ctx.query(paths)
