@@ -94,6 +94,19 @@ sbr_status sbr_subray_pattern(int32_t K, double *rho, double *phi, double *shrin
  * SBR_EINVAL if n < 1 or n > 20000; SBR_EOVERFLOW if cap_rays < N. */
 sbr_status sbr_raygen(sbr_ctx *ctx, int32_t n_div, float *dirs, int64_t cap_rays);
 
+/* §II.A (ref. 9): equidistant division, the launcher the paper compares against.  Ray
+ * points at equal intervals on each flat face of a regular polyhedron, projected onto the
+ * unit sphere: poly = 20 (the icosahedron of sbr_raygen, N = 10 n^2 + 2) or poly = 8 (the
+ * octahedron with vertices +-x, +-y, +-z, N = 4 n^2 + 2).  Order: vertices; edges (lower to
+ * higher vertex id) with points j = 1..n-1 at lo + (j/n)(hi - lo); per face (lowest vertex A
+ * first, outward orientation A, B, C) the interior points A + (i/n)(B - A) + (j/n)(C - A),
+ * i = 1..n-2, j = 1..n-1-i.  Writes float4 (x, y, z, 0) to the DEVICE buffer dirs.
+ * SBR_EINVAL for n < 1, n > 14000 or another poly; SBR_EOVERFLOW if cap_rays < N. */
+sbr_status sbr_raygen_equidistant(sbr_ctx *ctx, int32_t n_div, int32_t poly, float *dirs, int64_t cap_rays);
+/* Rays launched by launcher (0 = equiangular icosahedron, 20 = equidistant icosahedron,
+ * 8 = equidistant octahedron) at division level n; -1 if invalid. */
+int64_t sbr_num_rays_launcher(int32_t n_div, int32_t launcher);
+
 /* ---------------------------------------------------------------- scene */
 typedef struct {
     int64_t num_triangles;
@@ -141,6 +154,8 @@ typedef struct {
     int32_t block_threads;   /* multiple of 32, at most 128 (0 = 128) */
     int32_t refill_min;      /* a warp takes new rays once this many of its lanes are idle
                                 (1..32; 0 = 16: keeps a warp's rays neighbours in the lattice) */
+    int32_t launcher;        /* 0 = equiangular (§II.B), 20 / 8 = equidistant icosahedron /
+                                octahedron (§II.A); ray ids follow that launcher's order */
 } sbr_launch_params;
 
 #define SBR_LAUNCH_SYNC 1    /* synchronise at the end and report overflow / collisions */

@@ -84,6 +84,7 @@ def _load():
                                                      _d, _d]),
             "ora_unfold": (None, [_vp, ctypes.c_int, _i32, _d, _d, ctypes.c_double, ctypes.c_double, _d, _d]),
             "ora_num_threads": (ctypes.c_int, []),
+            "ora_equidistant": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, _d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -130,6 +131,16 @@ def icosahedron():
 def lattice(n: int) -> np.ndarray:
     out = np.zeros((num_rays(n), 3))
     _load().ora_lattice(n, _p(out))
+    return out
+
+
+def equidistant(n: int, poly: int = 20) -> np.ndarray:
+    """Equidistant division on the icosahedron (poly = 20) or octahedron (poly = 8)."""
+    N = (10 if poly == 20 else 4) * n * n + 2
+    out = np.zeros((N, 3))
+    c = _load().ora_equidistant(n, poly, _p(out))
+    if c != N:
+        raise ValueError("unknown polyhedron")
     return out
 
 
@@ -366,7 +377,7 @@ class PipelineResult:
 
 def sbr_pipeline(scene: Scene, txs, rxs, n: int, max_order: int, alpha: float, K: int, iters: int,
                  target: float = 0.0, ray_ids=None, want_margin=False, freq=2.4e9, keep_traces=False,
-                 refine_paths=True):
+                 refine_paths=True, launcher: int = 0):
     """The whole hot path in the paper's order (Fig. 4): equiangular launch, brute-force
     trace with reception, double-count removal, the precise algorithm, then the validity
     test and outputs.  The reception cone is alpha * theta_launch; the precise algorithm's
@@ -377,12 +388,13 @@ def sbr_pipeline(scene: Scene, txs, rxs, n: int, max_order: int, alpha: float, K
     txs = _f64(txs, (-1, 3))
     rxs = _f64(rxs, (-1, 3))
     cone = alpha * theta_launch(n)
+    all_dirs = equidistant(n, launcher) if launcher else None
     if ray_ids is None:
-        dirs = lattice(n)
+        dirs = lattice(n) if not launcher else all_dirs
         ids = None
     else:
         ids = np.asarray(ray_ids, np.int64)
-        dirs = lattice_ids(n, ids)
+        dirs = lattice_ids(n, ids) if not launcher else all_dirs[ids]
     paths, traces = [], []
     nseg = nrec = 0
     for t, tx in enumerate(txs):
@@ -392,7 +404,7 @@ def sbr_pipeline(scene: Scene, txs, rxs, n: int, max_order: int, alpha: float, K
         if keep_traces:
             traces.append(tr)
         for p in dedup(tr, t):
-            c0 = lattice_ids(n, [p["ray"]])[0]
+            c0 = lattice_ids(n, [p["ray"]])[0] if not launcher else all_dirs[p["ray"]]
             p["rough_dir"] = c0
             if refine_paths:
                 R0 = max(theta_launch(n), p["err"])

@@ -245,6 +245,67 @@ int64_t ora_face_points(int n, int f, double *pts, int *layer, int *index) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* §II.A: equidistant division (the prior-art launcher the paper compares with) */
+/* ------------------------------------------------------------------------- */
+/*
+ * Ray points at equal intervals on each flat face of a regular polyhedron, projected
+ * onto the unit sphere (§II.A, ref. 9).  poly = 20: the icosahedron of the equiangular
+ * lattice (same vertex, edge and face tables), N = 10 n^2 + 2; poly = 8: the octahedron
+ * with vertices +-x, +-y, +-z in that order, N = 4 n^2 + 2.  Order: vertices; edges
+ * (lower -> higher vertex id), points j = 1..n-1 at lo + (j/n)(hi - lo); per face (oriented,
+ * lowest vertex A first, then B, C) the interior points A + (i/n)(B - A) + (j/n)(C - A) for
+ * i = 1..n-2, j = 1..n-1-i.  Returns N, or -1 for an unknown polyhedron.
+ */
+static int octahedron_tables(vec3 V[6], int F[24], int E[24]) {
+    vec3 t[6] = {mk(1, 0, 0), mk(-1, 0, 0), mk(0, 1, 0), mk(0, -1, 0), mk(0, 0, 1), mk(0, 0, -1)};
+    int nf = 0, ne = 0;
+    for (int i = 0; i < 6; ++i) V[i] = t[i];
+    for (int i = 0; i < 6; ++i)
+        for (int j = i + 1; j < 6; ++j) {
+            if (fabs(dot(V[i], V[j])) > 1e-12) continue; /* antipodal pair */
+            E[2 * ne] = i; E[2 * ne + 1] = j; ++ne;
+            for (int k = j + 1; k < 6; ++k) {
+                if (fabs(dot(V[i], V[k])) > 1e-12 || fabs(dot(V[j], V[k])) > 1e-12) continue;
+                vec3 c = add(add(V[i], V[j]), V[k]);
+                int b = j, e = k;
+                if (dot(cross(sub(V[j], V[i]), sub(V[k], V[i])), c) < 0) { b = k; e = j; }
+                F[3 * nf] = i; F[3 * nf + 1] = b; F[3 * nf + 2] = e; ++nf;
+            }
+        }
+    return nf;
+}
+
+int64_t ora_equidistant(int n, int poly, double *dirs) {
+    vec3 V[12];
+    int F[60], E[60], nv, ne, nf;
+    if (poly == 20) {
+        double v[36];
+        ora_icosahedron(v, F, E);
+        for (int i = 0; i < 12; ++i) V[i] = ld(v + 3 * i);
+        nv = 12; ne = 30; nf = 20;
+    } else if (poly == 8) {
+        nf = octahedron_tables(V, F, E);
+        nv = 6; ne = 12;
+    } else {
+        return -1;
+    }
+    int64_t c = 0;
+    for (int i = 0; i < nv; ++i) st(dirs + 3 * c++, V[i]);
+    for (int e = 0; e < ne; ++e)
+        for (int j = 1; j < n; ++j) {
+            vec3 lo = V[E[2 * e]], hi = V[E[2 * e + 1]];
+            st(dirs + 3 * c++, unit(add(lo, scl(sub(hi, lo), (double)j / n))));
+        }
+    for (int f = 0; f < nf; ++f) {
+        vec3 A = V[F[3 * f]], B = V[F[3 * f + 1]], C = V[F[3 * f + 2]];
+        for (int i = 1; i <= n - 2; ++i)
+            for (int j = 1; j <= n - 1 - i; ++j)
+                st(dirs + 3 * c++, unit(add(A, add(scl(sub(B, A), (double)i / n), scl(sub(C, A), (double)j / n)))));
+    }
+    return c;
+}
+
+/* ------------------------------------------------------------------------- */
 /* §III.B: sub-ray patterns of the precise algorithm                          */
 /* ------------------------------------------------------------------------- */
 /*

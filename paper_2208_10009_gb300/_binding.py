@@ -37,7 +37,7 @@ class SceneInfo(_c.Structure):
 class LaunchParams(_c.Structure):
     _fields_ = [("n_div", _i32), ("max_order", _i32), ("rx_angle_scale", _f32), ("flags", _i32),
                 ("dump_stride", _i32), ("dump_faces", _vp), ("dump_cap", _i64), ("grid_blocks", _i32),
-                ("block_threads", _i32), ("refill_min", _i32)]
+                ("block_threads", _i32), ("refill_min", _i32), ("launcher", _i32)]
 
 
 class LaunchStats(_c.Structure):
@@ -82,6 +82,8 @@ SIGNATURES = {
     "sbr_theta_launch": (_f64, [_i32]),
     "sbr_subray_pattern": (_i32, [_i32, _pd, _pd, _pd]),
     "sbr_raygen": (_i32, [_vp, _i32, _vp, _i64]),
+    "sbr_raygen_equidistant": (_i32, [_vp, _i32, _i32, _vp, _i64]),
+    "sbr_num_rays_launcher": (_i64, [_i32, _i32]),
     "sbr_scene_upload": (_i32, [_vp, _pf, _i64, _pi32, _pi32, _i64, _pf, _i32, _c.POINTER(_vp)]),
     "sbr_scene_destroy": (_i32, [_vp, _vp]),
     "sbr_scene_get_info": (_i32, [_vp, _c.POINTER(SceneInfo)]),

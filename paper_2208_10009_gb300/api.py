@@ -141,6 +141,14 @@ class Context:
         self._check(self.lib.sbr_raygen(self.handle, n_div, _ptr(out), out.shape[0]))
         return out
 
+    def raygen_equidistant(self, n_div: int, poly: int = 20, out: torch.Tensor | None = None) -> torch.Tensor:
+        """§II.A equidistant division on the icosahedron (20) or octahedron (8)."""
+        N = self.lib.sbr_num_rays_launcher(n_div, poly)
+        if out is None:
+            out = torch.empty((max(N, 1), 4), dtype=torch.float32, device=f"cuda:{self.device}")
+        self._check(self.lib.sbr_raygen_equidistant(self.handle, n_div, poly, _ptr(out), out.shape[0]))
+        return out
+
     def scene_upload(self, verts, tris, tri_face, face_eps=None, nf=None) -> Scene:
         v = _host_f32(verts)
         t = np.ascontiguousarray(np.asarray(tris, np.int32).reshape(-1, 3))
@@ -178,7 +186,7 @@ class Context:
     def launch(self, scene: Scene, tx, rx: RxSet, paths: Paths, n_div: int, max_order: int,
                rx_angle_scale: float = 1.0, sync: bool = False, dump_stride: int = 0,
                dump: torch.Tensor | None = None, grid_blocks: int = 0, block_threads: int = 0,
-               timing: bool = False, refill_min: int = 0):
+               timing: bool = False, refill_min: int = 0, launcher: int = 0):
         """a1-a5: ray generation, trace with reception, double-count removal.  `tx` is an
         (ntx, 3) array on the host (numpy) or the device (torch)."""
         if isinstance(tx, torch.Tensor):
@@ -190,7 +198,7 @@ class Context:
         flags = (B.LAUNCH_SYNC if sync else 0) | (B.LAUNCH_TIMING if timing else 0)
         prm = B.LaunchParams(n_div, max_order, rx_angle_scale, flags, dump_stride,
                              _ptr(dump), 0 if dump is None else dump.numel(), grid_blocks, block_threads,
-                             refill_min)
+                             refill_min, launcher)
         self._check(self.lib.sbr_launch(self.handle, scene.handle, txp, ntx, rx.handle, ctypes.byref(prm),
                                         paths.handle))
         del keep

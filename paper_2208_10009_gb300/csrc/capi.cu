@@ -70,6 +70,13 @@ struct Carver {
 
 int64_t rays_for(int n) { return 10LL * n * n + 2; }
 
+int64_t rays_for_launcher(int n, int launcher) {
+    if (n < 1) return -1;
+    if (launcher == 0 || launcher == 20) return 10LL * n * n + 2;
+    if (launcher == 8) return 4LL * n * n + 2;
+    return -1;
+}
+
 float bits_as_float(int i) {
     float f;
     std::memcpy(&f, &i, sizeof(f));
@@ -115,8 +122,45 @@ sbr_status ensure_lattice(sbr_ctx *ctx, int n) {
     return SBR_OK;
 }
 
-sbr_status ensure_dirs(sbr_ctx *ctx, int n) {
-    int64_t N = rays_for(n);
+sbr_status ensure_poly(sbr_ctx *ctx, int poly, int n) {
+    if (ctx->poly_kind != poly || !ctx->poly_mem) {
+        std::vector<float4> v;
+        std::vector<int2> e;
+        std::vector<int4> f;
+        if (!build_polyhedron(poly, v, e, f)) return fail(ctx, SBR_EINVAL, "equidistant: poly must be 20 or 8");
+        float4 *dv;
+        int2 *de;
+        int4 *df;
+        Carver cv;
+        cv.add(&dv, v.size());
+        cv.add(&de, e.size());
+        cv.add(&df, f.size());
+        if (ctx->poly_bytes < cv.total) {
+            dev_free(ctx, ctx->poly_mem, ctx->poly_bytes);
+            ctx->poly_mem = dev_alloc(ctx, cv.total);
+            ctx->poly_bytes = ctx->poly_mem ? cv.total : 0;
+            if (!ctx->poly_mem) return fail(ctx, SBR_ENOMEM, "equidistant tables: allocation failed");
+        }
+        cv.bind(ctx->poly_mem);
+        SBR_CUDA(cudaMemcpyAsync(dv, v.data(), v.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
+        SBR_CUDA(cudaMemcpyAsync(de, e.data(), e.size() * sizeof(int2), cudaMemcpyHostToDevice, ctx->stream));
+        SBR_CUDA(cudaMemcpyAsync(df, f.data(), f.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+        SBR_CUDA(cudaStreamSynchronize(ctx->stream));
+        ctx->poly.v = dv;
+        ctx->poly.edges = de;
+        ctx->poly.faces = df;
+        ctx->poly.nv = (int)v.size();
+        ctx->poly.ne = (int)e.size();
+        ctx->poly.nf = (int)f.size();
+        ctx->poly_kind = poly;
+    }
+    ctx->poly.n = n;
+    return SBR_OK;
+}
+
+sbr_status ensure_dirs(sbr_ctx *ctx, int n, int launcher) {
+    int64_t N = rays_for_launcher(n, launcher);
+    if (N < 0) return fail(ctx, SBR_EINVAL, "launcher must be 0 (equiangular), 20 or 8 (equidistant)");
     size_t need = (size_t)N * sizeof(float4);
     if (ctx->dirs_bytes < need) {
         dev_free(ctx, ctx->dirs, ctx->dirs_bytes);
@@ -125,10 +169,17 @@ sbr_status ensure_dirs(sbr_ctx *ctx, int n) {
         ctx->dirs_valid = false;
         if (!ctx->dirs) return fail(ctx, SBR_ENOMEM, "ray directions: allocation failed");
     }
-    sbr_status st = ensure_lattice(ctx, n);
-    if (st != SBR_OK) return st;
-    SBR_CUDA(launch_raygen(ctx->lattice, static_cast<float4 *>(ctx->dirs), N, ctx->stream));
+    if (launcher == 0) {
+        sbr_status st = ensure_lattice(ctx, n);
+        if (st != SBR_OK) return st;
+        SBR_CUDA(launch_raygen(ctx->lattice, static_cast<float4 *>(ctx->dirs), N, ctx->stream));
+    } else {
+        sbr_status st = ensure_poly(ctx, launcher, n);
+        if (st != SBR_OK) return st;
+        SBR_CUDA(launch_raygen_equidistant(ctx->poly, static_cast<float4 *>(ctx->dirs), N, ctx->stream));
+    }
     ctx->dirs_n = n;
+    ctx->dirs_launcher = launcher;
     ctx->dirs_valid = true;
     return SBR_OK;
 }
@@ -190,6 +241,21 @@ const char *sbr_last_error(const sbr_ctx *ctx) { return ctx ? ctx->last_error.c_
 
 int64_t sbr_num_rays(int32_t n) { return n < 1 ? -1 : rays_for(n); }
 
+int64_t sbr_num_rays_launcher(int32_t n, int32_t launcher) { return rays_for_launcher(n, launcher); }
+
+sbr_status sbr_raygen_equidistant(sbr_ctx *ctx, int32_t n, int32_t poly, float *dirs, int64_t cap) {
+    if (!ctx || !dirs) return fail(ctx, SBR_EINVAL, "sbr_raygen_equidistant: null argument");
+    if (n < 1 || n > 14000) return fail(ctx, SBR_EINVAL, "sbr_raygen_equidistant: n_div out of range [1, 14000]");
+    if (poly != 20 && poly != 8) return fail(ctx, SBR_EINVAL, "sbr_raygen_equidistant: poly must be 20 or 8");
+    int64_t N = rays_for_launcher(n, poly);
+    if (cap < N) return fail(ctx, SBR_EOVERFLOW, "sbr_raygen_equidistant: buffer smaller than the ray count");
+    DeviceGuard g(ctx->device);
+    sbr_status st = ensure_poly(ctx, poly, n);
+    if (st != SBR_OK) return st;
+    SBR_CUDA(launch_raygen_equidistant(ctx->poly, reinterpret_cast<float4 *>(dirs), N, ctx->stream));
+    return SBR_OK;
+}
+
 double sbr_theta_launch(int32_t n) { return n < 1 ? -1.0 : std::acos(1.0 / std::sqrt(5.0)) / (std::sqrt(3.0) * n); }
 
 sbr_status sbr_subray_pattern(int32_t K, double *rho, double *phi, double *shrink) {
@@ -232,6 +298,7 @@ sbr_status sbr_ctx_destroy(sbr_ctx *ctx) {
     DeviceGuard g(ctx->device);
     dev_free(ctx, ctx->dirs, ctx->dirs_bytes);
     dev_free(ctx, ctx->lattice_mem, ctx->lattice_bytes);
+    dev_free(ctx, ctx->poly_mem, ctx->poly_bytes);
     cudaStreamSynchronize(ctx->stream);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -547,9 +614,11 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
         return fail(ctx, SBR_EINVAL, "sbr_launch: max_order out of range [0, 8]");
     if (!(prm->rx_angle_scale > 0.0f) || !std::isfinite(prm->rx_angle_scale))
         return fail(ctx, SBR_EINVAL, "sbr_launch: rx_angle_scale must be positive");
+    if (rays_for_launcher(prm->n_div, prm->launcher) < 0)
+        return fail(ctx, SBR_EINVAL, "sbr_launch: launcher must be 0 (equiangular), 20 or 8 (equidistant)");
     if (prm->dump_stride > 0) {
         if (!prm->dump_faces) return fail(ctx, SBR_EINVAL, "sbr_launch: dump_faces is null");
-        int64_t per = (rays_for(prm->n_div) + prm->dump_stride - 1) / prm->dump_stride;
+        int64_t per = (rays_for_launcher(prm->n_div, prm->launcher) + prm->dump_stride - 1) / prm->dump_stride;
         if (prm->dump_cap < (int64_t)ntx * per * (prm->max_order + 1))
             return fail(ctx, SBR_EINVAL, "sbr_launch: dump_cap smaller than ntx * ceil(N / stride) * (max_order + 1)");
     }
@@ -560,10 +629,10 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     if (timing && !ctx->ev[0])
         for (auto &e : ctx->ev) SBR_CUDA(cudaEventCreate(&e));
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
-    st = ensure_dirs(ctx, prm->n_div);
+    st = ensure_dirs(ctx, prm->n_div, prm->launcher);
     if (st != SBR_OK) return st;
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
-    const int64_t N = rays_for(prm->n_div);
+    const int64_t N = rays_for_launcher(prm->n_div, prm->launcher);
     SBR_CUDA(cudaMemsetAsync(paths->counters, 0, kNumCounters * sizeof(long long), ctx->stream));
     TraceArgs a;
     a.scene = scene->dev;
@@ -606,6 +675,7 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     paths->ntx = ntx;
     paths->nrx = rx->dev.nrx;
     paths->n_div = prm->n_div;
+    paths->launcher = prm->launcher;
     paths->max_order = prm->max_order;
     paths->rx = rx;
     paths->alpha = prm->rx_angle_scale;
@@ -628,7 +698,7 @@ sbr_status sbr_launch_get_stats(sbr_ctx *ctx, const sbr_paths *paths, sbr_launch
     long long c[kNumCounters];
     SBR_CUDA(cudaMemcpyAsync(c, paths->counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
     SBR_CUDA(cudaStreamSynchronize(ctx->stream));
-    out->rays = (int64_t)paths->ntx * rays_for(std::max(paths->n_div, 1));
+    out->rays = (int64_t)paths->ntx * std::max<int64_t>(rays_for_launcher(std::max(paths->n_div, 1), paths->launcher), 0);
     out->segments = c[kSegments];
     out->node_visits = c[kNodeVisits];
     out->tri_tests = c[kTriTests];

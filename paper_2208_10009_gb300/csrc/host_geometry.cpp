@@ -388,6 +388,44 @@ void build_lattice_tables(int n, std::vector<float4> &ico, std::vector<int2> &ed
     }
 }
 
+// ============================================================================ equidistant
+bool build_polyhedron(int poly, std::vector<float4> &v, std::vector<int2> &e, std::vector<int4> &f) {
+    std::vector<D3> V;
+    if (poly == 20) {
+        const double g = 0.5 * (1.0 + std::sqrt(5.0));
+        const double raw[12][3] = {{0, 1, g},  {0, -1, g},  {0, 1, -g},  {0, -1, -g}, {1, g, 0},  {-1, g, 0},
+                                   {1, -g, 0}, {-1, -g, 0}, {g, 0, 1},  {-g, 0, 1},  {g, 0, -1}, {-g, 0, -1}};
+        for (auto &r : raw) V.push_back(normed(d3(r[0], r[1], r[2])));
+    } else if (poly == 8) {
+        const double raw[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+        for (auto &r : raw) V.push_back(d3(r[0], r[1], r[2]));
+    } else {
+        return false;
+    }
+    // neighbours subtend the polyhedron's smallest vertex angle
+    double amin = 10.0;
+    for (size_t i = 0; i < V.size(); ++i)
+        for (size_t j = i + 1; j < V.size(); ++j) amin = std::min(amin, arc(V[i], V[j]));
+    auto adj = [&](int i, int j) { return std::fabs(arc(V[i], V[j]) - amin) < 1e-9; };
+    v.clear();
+    e.clear();
+    f.clear();
+    for (auto &p : V) v.push_back(make_float4((float)p.x, (float)p.y, (float)p.z, 0.0f));
+    int n = (int)V.size();
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            if (!adj(i, j)) continue;
+            e.push_back(make_int2(i, j));
+            for (int k = j + 1; k < n; ++k) {
+                if (!adj(i, k) || !adj(j, k)) continue;
+                D3 c = V[i] + V[j] + V[k];
+                bool ccw = dot3(cross3(V[j] - V[i], V[k] - V[i]), c) > 0.0;
+                f.push_back(make_int4(i, ccw ? j : k, ccw ? k : j, 0));
+            }
+        }
+    return true;
+}
+
 // ============================================================================ sub-rays
 // Sub-cone centres covering a cone of half-angle 1 (fractions of R) and the shrink factor
 // (sub-cone half-angle / R).  K = 6 is the paper's ring of six at R/sqrt(3) (Fig. 5,

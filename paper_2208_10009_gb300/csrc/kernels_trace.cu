@@ -73,6 +73,58 @@ cudaError_t launch_raygen(const LatticeDev &lat, float4 *dirs, int64_t N, cudaSt
     return cudaGetLastError();
 }
 
+// §II.A equidistant division: flat-face points projected onto the sphere.
+// interior rows before row i of a face: sum_{i'=1}^{i-1} (n - 1 - i')
+__device__ __forceinline__ long long row_prefix(int n, long long i) { return (i - 1) * (n - 1) - (i - 1) * i / 2; }
+
+__global__ void raygen_equidistant_kernel(PolyDev P, float4 *__restrict__ dirs, long long N) {
+    const int n = P.n;
+    const long long n_edge = (long long)P.ne * (n - 1);
+    const long long per_face = (long long)(n - 1) * (n - 2) / 2;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N;
+         id += (long long)gridDim.x * blockDim.x) {
+        float3 p;
+        if (id < P.nv) {
+            p = f3(__ldg(P.v + id));
+        } else if (id < P.nv + n_edge) {
+            long long r = id - P.nv;
+            int e = (int)(r / (n - 1)), j = (int)(r % (n - 1)) + 1;
+            int2 ed = __ldg(P.edges + e);
+            float3 lo = f3(__ldg(P.v + ed.x)), hi = f3(__ldg(P.v + ed.y));
+            p = lo + (hi - lo) * ((float)j / (float)n);
+        } else {
+            long long r = id - P.nv - n_edge;
+            int f = (int)(r / per_face);
+            long long q = r % per_face;
+            // row i >= 1 with row_prefix(i) <= q < row_prefix(i + 1): estimate, then fix
+            float B = (float)n - 1.5f;
+            float disc = fmaxf(B * B - 2.0f * (float)q, 0.0f);
+            long long i = (long long)(B - sqrtf(disc)) + 1;
+            if (i < 1) i = 1;
+            if (i > n - 2) i = n - 2;
+            while (i > 1 && row_prefix(n, i) > q) --i;
+            while (i < n - 2 && row_prefix(n, i + 1) <= q) ++i;
+            int j = (int)(q - row_prefix(n, i)) + 1;
+            int4 fc = __ldg(P.faces + f);
+            float3 A = f3(__ldg(P.v + fc.x)), Bv = f3(__ldg(P.v + fc.y)), C = f3(__ldg(P.v + fc.z));
+            p = A + (Bv - A) * ((float)i / (float)n) + (C - A) * ((float)j / (float)n);
+        }
+        float inv = 1.0f / sqrtf(dot(p, p));
+        dirs[id] = make_float4(p.x * inv, p.y * inv, p.z * inv, 0.0f);
+    }
+}
+
+cudaError_t launch_raygen_equidistant(const PolyDev &P, float4 *dirs, int64_t N, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long want = (N + 255) / 256;
+    int grid = (int)(want < (long long)sms * 16 ? want : (long long)sms * 16);
+    if (grid < 1) grid = 1;
+    raygen_equidistant_kernel<<<grid, 256, 0, s>>>(P, dirs, (long long)N);
+    return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------------------- a2-a4
 struct LaneRay {
     float3 o, d;

@@ -172,7 +172,7 @@ extern "C" sbr_status sbr_dedup_noalloc(sbr_ctx *ctx, const sbr_paths *src, sbr_
         return na_fail(ctx, SBR_EINVAL, "sbr_dedup_noalloc: the container's record capacity " +
                                             std::to_string(src->record_cap) + " exceeds the fixed maximum of " +
                                             std::to_string(kMaxRecords) + " records");
-    if (src->n_div < 1 || !ctx->dirs || ctx->dirs_n != src->n_div)
+    if (src->n_div < 1 || !ctx->dirs || ctx->dirs_n != src->n_div || ctx->dirs_launcher != src->launcher)
         return na_fail(ctx, SBR_EINVAL, "sbr_dedup_noalloc: the container holds no launch whose ray directions "
                                         "are still current on this context");
     if (ctx->device < 0 || ctx->device >= 128) return na_fail(ctx, SBR_EINVAL, "sbr_dedup_noalloc: device id");

@@ -88,6 +88,14 @@ struct LatticeDev {
     float edge_angle;         // theta_0
 };
 
+// Flat-face tables for the equidistant launcher.
+struct PolyDev {
+    const float4 *v;          // vertices (unit)
+    const int2 *edges;        // (lo, hi)
+    const int4 *faces;        // (A, B, C, -) outward, lowest id first
+    int nv, ne, nf, n;
+};
+
 }  // namespace sbr
 
 // ---------------------------------------------------------------- host handle structs
@@ -110,6 +118,12 @@ struct sbr_ctx {
     size_t lattice_bytes = 0;
     int lattice_n = 0;
     sbr::LatticeDev lattice{};
+    int dirs_launcher = 0;
+    // equidistant launcher tables
+    void *poly_mem = nullptr;
+    size_t poly_bytes = 0;
+    int poly_kind = 0;
+    sbr::PolyDev poly{};
     // kernel timing events (SBR_LAUNCH_TIMING)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
@@ -146,7 +160,7 @@ struct sbr_paths {
     int32_t tx_cap = 0;
     void *tx_mem = nullptr;
     size_t tx_bytes = 0;
-    int32_t ntx = 0, nrx = 0, n_div = 0, max_order = 0;
+    int32_t ntx = 0, nrx = 0, n_div = 0, max_order = 0, launcher = 0;
     const sbr_rxset *rx = nullptr;
     float alpha = 1.0f;
     bool timed = false;                    // last launch recorded kernel events
@@ -176,9 +190,12 @@ void build_lattice_tables(int n, std::vector<float4> &ico, std::vector<int2> &ed
                           std::vector<float4> &layers, int &nl);
 // Sub-ray pattern constants.
 int subray_pattern(int K, double *rho, double *phi, double *shrink);
+// Vertex / edge / face tables of the icosahedron (poly 20) or octahedron (poly 8).
+bool build_polyhedron(int poly, std::vector<float4> &v, std::vector<int2> &e, std::vector<int4> &f);
 
 // kernels (kernels_*.cu)
 cudaError_t launch_raygen(const LatticeDev &lat, float4 *dirs, int64_t N, cudaStream_t s);
+cudaError_t launch_raygen_equidistant(const PolyDev &p, float4 *dirs, int64_t N, cudaStream_t s);
 
 struct TraceArgs {
     SceneDev scene;

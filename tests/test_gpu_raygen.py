@@ -44,3 +44,40 @@ def test_raygen_rejects_bad_sizes(gpu_ctx):
         gpu_ctx.raygen(2, small)
     with pytest.raises(api.SbrError):
         gpu_ctx.raygen(0, small)
+
+
+@pytest.mark.parametrize("poly", [20, 8])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 21, 64, 250])
+def test_equidistant_matches_oracle(gpu_ctx, oracle_mod, poly, n):
+    d = gpu_ctx.raygen_equidistant(n, poly).cpu().numpy()
+    want = oracle_mod.equidistant(n, poly)
+    assert d.shape == (len(want), 4)
+    assert _angles(d[:, :3].astype(np.float64), want).max() < TOL
+
+
+def test_equidistant_launch_matches_oracle(gpu_ctx, oracle_mod):
+    """The whole path on the equidistant icosahedron (launcher 20): rough paths after
+    double-count removal equal the oracle's, refined paths reach the image method."""
+    from paper_2208_10009_gb300 import scenes
+    sc, tx, rx = scenes.shoebox_config()
+    scene = gpu_ctx.scene_from(sc)
+    rxs = gpu_ctx.rx_upload(rx)
+    paths = gpu_ctx.paths_create(1 << 16, 1 << 12)
+    sq3 = float(np.sqrt(3.0))
+    gpu_ctx.launch(scene, tx, rxs, paths, 48, 3, rx_angle_scale=sq3, sync=True, launcher=20)
+    rough = gpu_ctx.query(paths)
+    S = oracle_mod.Scene.from_generated(sc)
+    ora = oracle_mod.sbr_pipeline(S, tx, rx, 48, 3, sq3, 9, 0, refine_paths=False, launcher=20)
+    g = {tuple(int(f) for f in r["faces"][: r["order"]]) for r in rough}
+    o = {p["faces"] for p in ora.paths}
+    assert g == o
+    gpu_ctx.refine(scene, paths, 10, 9)
+    got = gpu_ctx.query(paths)
+    im = {p["faces"]: p for p in oracle_mod.image_enumerate(S, tx[0], rx[0], 3)}
+    for r in got:
+        key = tuple(int(f) for f in r["faces"][: r["order"]])
+        if r["valid"]:
+            a = np.asarray(r["dir"], np.float64)
+            assert np.arctan2(np.linalg.norm(np.cross(a, im[key]["aod_dir"])), a @ im[key]["aod_dir"]) < np.radians(0.01)
+    for h in (paths, rxs, scene):
+        h.close()
