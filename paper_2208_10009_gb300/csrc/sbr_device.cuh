@@ -32,11 +32,14 @@ __device__ __forceinline__ dvec3 dcross(dvec3 a, dvec3 b) {
 }
 __device__ __forceinline__ double dnorm(dvec3 a) { return sqrt(ddot(a, a)); }
 
-// Per-ray precomputation for the slab test and the watertight triangle test.
+// Per-ray precomputation for the slab test and the watertight triangle test.  The
+// triangle test's axis permutation and shear are folded into three vectors, so that a
+// vertex's sheared coordinates are plain dot products (FMA pipe, no per-component
+// selects): with kz the dominant axis of d and (kx, ky) the other two in winding order,
+// mx = e_kx - (d_kx / d_kz) e_kz, my = e_ky - (d_ky / d_kz) e_kz, mz = e_kz / d_kz.
 struct RayPre {
     float3 o, d, inv;
-    int kx, ky, kz;
-    float Sx, Sy, Sz;
+    float3 mx, my, mz;
     int nx, ny, nz;   // 1 where 1/d < 0: the near slab plane is the box's hi side
 };
 
@@ -61,13 +64,13 @@ __device__ __forceinline__ RayPre make_ray(float3 o, float3 d) {
         kx = ky;
         ky = t;
     }
-    r.kx = kx;
-    r.ky = ky;
-    r.kz = kz;
-    float dz = comp(d, kz);
-    r.Sx = comp(d, kx) / dz;
-    r.Sy = comp(d, ky) / dz;
-    r.Sz = 1.0f / dz;
+    const float sz = 1.0f / comp(d, kz);
+    const float sx = comp(d, kx) * sz, sy = comp(d, ky) * sz;
+    r.mx = make_float3(kx == 0 ? 1.0f : (kz == 0 ? -sx : 0.0f), kx == 1 ? 1.0f : (kz == 1 ? -sx : 0.0f),
+                       kx == 2 ? 1.0f : (kz == 2 ? -sx : 0.0f));
+    r.my = make_float3(ky == 0 ? 1.0f : (kz == 0 ? -sy : 0.0f), ky == 1 ? 1.0f : (kz == 1 ? -sy : 0.0f),
+                       ky == 2 ? 1.0f : (kz == 2 ? -sy : 0.0f));
+    r.mz = make_float3(kz == 0 ? sz : 0.0f, kz == 1 ? sz : 0.0f, kz == 2 ? sz : 0.0f);
     return r;
 }
 
@@ -98,10 +101,9 @@ __device__ __forceinline__ int slab2(const float4 *node, const RayPre &r, float 
 // Returns t, or a negative value on a miss.
 __device__ __forceinline__ float tri_watertight(const RayPre &r, float4 A4, float4 B4, float4 C4) {
     float3 A = f3(A4) - r.o, B = f3(B4) - r.o, C = f3(C4) - r.o;
-    float Az = comp(A, r.kz), Bz = comp(B, r.kz), Cz = comp(C, r.kz);
-    float Ax = comp(A, r.kx) - r.Sx * Az, Ay = comp(A, r.ky) - r.Sy * Az;
-    float Bx = comp(B, r.kx) - r.Sx * Bz, By = comp(B, r.ky) - r.Sy * Bz;
-    float Cx = comp(C, r.kx) - r.Sx * Cz, Cy = comp(C, r.ky) - r.Sy * Cz;
+    float Ax = dot(A, r.mx), Ay = dot(A, r.my), Az = dot(A, r.mz);
+    float Bx = dot(B, r.mx), By = dot(B, r.my), Bz = dot(B, r.mz);
+    float Cx = dot(C, r.mx), Cy = dot(C, r.my), Cz = dot(C, r.mz);
     float U = Cx * By - Cy * Bx;
     float V = Ax * Cy - Ay * Cx;
     float W = Bx * Ay - By * Ax;
@@ -113,7 +115,7 @@ __device__ __forceinline__ float tri_watertight(const RayPre &r, float4 A4, floa
     if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
     float det = U + V + W;
     if (det == 0.0f) return -1.0f;
-    float T = U * (r.Sz * Az) + V * (r.Sz * Bz) + W * (r.Sz * Cz);
+    float T = U * Az + V * Bz + W * Cz;   // mz carries the 1 / d_kz scale
     return T / det;
 }
 
