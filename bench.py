@@ -303,7 +303,7 @@ def run_gpu(args):
                         "flops_per_launch": flops},
            "clocks": clocks, "gpu_launches": 6 * args.steps, "wall_s": t_wall, "e2e": e2e}
     if rank == 0 and not args.no_cpu_baseline:
-        stride = 7
+        stride = 4
         s, g, dt, nr, cores = cpu_oracle_sample(sc, tx, rx, stride)
         out["cpu_baseline"] = {"value": s / dt, "unit": "ray-bounces/s", "cores": cores, "kind": "oracle",
                                "sample": f"every {stride}th ray id ({nr} rays, {s} ray-bounces): brute-force FP64 "

@@ -17,42 +17,43 @@ __device__ __forceinline__ float3 arc_point(float3 u, float3 v, float om, int j,
     return p * inv;
 }
 
-// interior points of layers 1..a of a face: S(a) = sum_{a'=1..a} 3(n - 3a')
-__device__ __forceinline__ long long layer_prefix(int n, long long a) { return (6LL * n * a - 9LL * a * a - 9LL * a) / 2; }
+// interior points of layers 1..a of a face: S(a) = sum_{a'=1..a} 3(n - 3a') (fits 32 bits
+// for n <= 14000)
+__device__ __forceinline__ int layer_prefix(int n, int a) { return (6 * n * a - 9 * a * a - 9 * a) / 2; }
 
-__global__ void raygen_kernel(LatticeDev L, float4 *__restrict__ dirs, long long N) {
+// One thread per ray; 32-bit index arithmetic (N < 2^31 for the supported n).
+__global__ void raygen_kernel(LatticeDev L, float4 *__restrict__ dirs, int N) {
     const int n = L.n;
-    const long long n_edge = 30LL * (n - 1);
-    const long long per_face = (long long)(n - 1) * (n - 2) / 2;
-    const long long layer_pts = layer_prefix(n, L.nl - 1);   // points on layers 1..nl-1
-    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N;
-         id += (long long)gridDim.x * blockDim.x) {
+    const int n_edge = 30 * (n - 1);
+    const int per_face = (n - 1) * (n - 2) / 2;
+    const int layer_pts = layer_prefix(n, L.nl - 1);   // points on layers 1..nl-1
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < N; id += gridDim.x * blockDim.x) {
         float3 d;
         if (id < 12) {
             d = f3(__ldg(L.ico + id));
         } else if (id < 12 + n_edge) {
-            long long r = id - 12;
-            int e = (int)(r / (n - 1)), j = (int)(r % (n - 1)) + 1;
+            int r = id - 12;
+            int e = r / (n - 1), j = r - e * (n - 1) + 1;
             int2 ed = __ldg(L.edges + e);
             d = arc_point(f3(__ldg(L.ico + ed.x)), f3(__ldg(L.ico + ed.y)), L.edge_angle, j, n);
         } else {
-            long long r = id - 12 - n_edge;
-            int f = (int)(r / per_face);
-            long long q = r % per_face;
+            int r = id - 12 - n_edge;
+            int f = r / per_face;
+            int q = r - f * per_face;
             if (q >= layer_pts) {
                 d = f3(__ldg(L.centre + f));   // n = 0 mod 3: the face centre ray
             } else {
                 // layer a >= 1 with S(a-1) <= q < S(a): estimate from the quadratic, then fix
                 float B = 3.0f * n - 4.5f;
                 float disc = fmaxf(B * B - 18.0f * (float)q, 0.0f);
-                long long a = (long long)((B - sqrtf(disc)) / 9.0f) + 1;
+                int a = (int)((B - sqrtf(disc)) / 9.0f) + 1;
                 if (a < 1) a = 1;
                 if (a > L.nl - 1) a = L.nl - 1;
                 while (a > 1 && layer_prefix(n, a - 1) > q) --a;
                 while (layer_prefix(n, a) <= q) ++a;
-                long long b = q - layer_prefix(n, a - 1);
-                int m = n - 3 * (int)a;
-                int e = (int)(b / m), j = (int)(b % m);
+                int b = q - layer_prefix(n, a - 1);
+                int m = n - 3 * a;
+                int e = b / m, j = b - e * m;
                 const float4 *W = L.layers + ((size_t)f * L.nl + a) * 3;
                 float4 w0 = __ldg(W + e), w1 = __ldg(W + (e == 2 ? 0 : e + 1));
                 d = arc_point(f3(w0), f3(w1), w0.w, j, m);
@@ -69,7 +70,7 @@ cudaError_t launch_raygen(const LatticeDev &lat, float4 *dirs, int64_t N, cudaSt
     long long want = (N + 255) / 256;
     int grid = (int)(want < (long long)sms * 16 ? want : (long long)sms * 16);
     if (grid < 1) grid = 1;
-    raygen_kernel<<<grid, 256, 0, s>>>(lat, dirs, (long long)N);
+    raygen_kernel<<<grid, 256, 0, s>>>(lat, dirs, (int)N);
     return cudaGetLastError();
 }
 

@@ -95,6 +95,17 @@ __device__ __forceinline__ int slab2(const float4 *node, const RayPre &r, float 
     return (n0 <= f0 ? 1 : 0) | (n1 <= f1 ? 2 : 0);
 }
 
+// Three-input min / max (one instruction each on sm_100 and later).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
 // Watertight ray/triangle intersection (Woop, Benthin, Wald, JCGT 2013): edge functions in a
 // sheared, permuted frame; an exactly-zero edge function is re-evaluated in double so
 // that rays through a shared edge or vertex hit at least one of the triangles.
@@ -107,12 +118,13 @@ __device__ __forceinline__ float tri_watertight(const RayPre &r, float4 A4, floa
     float U = Cx * By - Cy * Bx;
     float V = Ax * Cy - Ay * Cx;
     float W = Bx * Ay - By * Ax;
-    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+    if (min3f(fabsf(U), fabsf(V), fabsf(W)) == 0.0f) {
         U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
         V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
         W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
     }
-    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
+    // outside if the edge functions have mixed signs
+    if (min3f(U, V, W) < 0.0f && max3f(U, V, W) > 0.0f) return -1.0f;
     float det = U + V + W;
     if (det == 0.0f) return -1.0f;
     float T = U * Az + V * Bz + W * Cz;   // mz carries the 1 / d_kz scale
@@ -175,17 +187,6 @@ __device__ __forceinline__ int closest_hit(const SceneDev &S, const RayPre &r, f
     return best;
 }
 
-// Three-input min / max (one instruction each on sm_100 and later).
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-    float d;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
-}
-__device__ __forceinline__ float min3f(float a, float b, float c) {
-    float d;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
-    return d;
-}
 // Two FMAs in one packed f32x2 instruction: (a.x * b + c, a.y * b + c).
 __device__ __forceinline__ float2 fma2s(float ax, float ay, float b, float c) {
     float2 r;
@@ -251,18 +252,14 @@ __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, 
                 dist[c] = tn <= tf ? tn : INFINITY;
             }
             float d0 = dist[0], d1 = dist[1], d2 = dist[2], d3 = dist[3];
-            int r0 = refs.x, r1 = refs.y, r2 = refs.z, r3 = refs.w;
-            cswap(d0, r0, d1, r1);
-            cswap(d2, r2, d3, r3);
-            cswap(d0, r0, d2, r2);
-            cswap(d1, r1, d3, r3);
-            cswap(d1, r1, d2, r2);
-            int h = (d0 < INFINITY) + (d1 < INFINITY) + (d2 < INFINITY) + (d3 < INFINITY);
-            if (h > 0) {
-                if (h > 3) stack[sp++] = r3;
-                if (h > 2) stack[sp++] = r2;
-                if (h > 1) stack[sp++] = r1;
-                node = r0;
+            float dmin = fminf(min3f(d0, d1, d2), d3);
+            if (dmin < INFINITY) {
+                int pick = d0 == dmin ? 0 : (d1 == dmin ? 1 : (d2 == dmin ? 2 : 3));
+                if (d3 < INFINITY && pick != 3) stack[sp++] = refs.w;
+                if (d2 < INFINITY && pick != 2) stack[sp++] = refs.z;
+                if (d1 < INFINITY && pick != 1) stack[sp++] = refs.y;
+                if (d0 < INFINITY && pick != 0) stack[sp++] = refs.x;
+                node = pick == 0 ? refs.x : (pick == 1 ? refs.y : (pick == 2 ? refs.z : refs.w));
                 continue;
             }
         } else {
