@@ -27,9 +27,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ray-bounces/s and refined paths/s at <=0.01 deg AOD/AOA error; % of roofline"
-WORKLOAD = dict(workload="urban canyon: 20x20 box city + ground (~10k tris), 1 Tx x 256 Rx, n=700, order 6, "
-                         "alpha=sqrt(3), 6 refinement iterations, K=9",
-                n_div=700, max_order=6, alpha=float(np.sqrt(3.0)), iters=6, K=9)
+WORKLOADS = {
+    "canyon": dict(workload="urban canyon: 20x20 box city + ground (~10k tris), 1 Tx x 256 Rx, n=700, order 6, "
+                            "alpha=sqrt(3), 6 refinement iterations, K=9",
+                   gen="urban_canyon", n_div=700, max_order=6, alpha=float(np.sqrt(3.0)), iters=6, K=9, target=0.0),
+    "office": dict(workload="office: 40x30x4 m shell + 400 boxes (~55k tris), 16 Tx x 1024 Rx, n=128, order 6, "
+                            "alpha=sqrt(3), refinement K=16 with early stop at 0.01 deg, cap 8",
+                   gen="office", n_div=128, max_order=6, alpha=float(np.sqrt(3.0)), iters=8, K=16,
+                   target=float(np.radians(0.01))),
+    "city": dict(workload="large city: 60x60 extruded polygons + 700^2 terrain (~1.07M tris), 4 Tx x 4096 Rx, "
+                          "n=2200, order 8, alpha=sqrt(3), 16 refinement iterations, K=9",
+                 gen="large_city", n_div=2200, max_order=8, alpha=float(np.sqrt(3.0)), iters=16, K=9, target=0.0),
+    "shoebox": dict(workload="shoebox: 10x8x3 m room (12 tris), 1 Tx x 1 Rx, n=64, order 3, alpha=sqrt(3), "
+                             "5 refinement iterations, K=9",
+                    gen="shoebox_config", n_div=64, max_order=3, alpha=float(np.sqrt(3.0)), iters=5, K=9, target=0.0),
+}
+WORKLOAD = WORKLOADS["canyon"]
 ACC_DEG = 0.01
 # FLOPs per unit of the trace kernel (counted from the kernel source): a 4-wide node visit
 # (four child slab tests of 6 FMA each), one watertight triangle test, one receiver
@@ -194,8 +207,9 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc, tx, rx = scenes.urban_canyon()
-    n, order, alpha, iters, K = (WORKLOAD[k] for k in ("n_div", "max_order", "alpha", "iters", "K"))
+    W = WORKLOADS[args.workload]
+    sc, tx, rx = getattr(scenes, W["gen"])()
+    n, order, alpha, iters, K, target = (W[k] for k in ("n_div", "max_order", "alpha", "iters", "K", "target"))
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     ctx = api.Context(local, stream=stream)
@@ -203,10 +217,20 @@ def run_gpu(args):
     rxs = ctx.rx_upload(rx)
     tx_dev = torch.as_tensor(tx.astype(np.float32), device=dev)
     # size the containers from one synchronous launch
-    probe = ctx.paths_create(1 << 20, 1 << 18)
-    ctx.launch(scene, tx_dev, rxs, probe, n, order, rx_angle_scale=alpha, sync=True)
-    st0 = ctx.launch_stats(probe)
-    probe.close()
+    cap_r, cap_p = 1 << 20, 1 << 18
+    while True:
+        probe = ctx.paths_create(cap_r, cap_p)
+        try:
+            ctx.launch(scene, tx_dev, rxs, probe, n, order, rx_angle_scale=alpha, sync=True)
+            st0 = ctx.launch_stats(probe)
+            break
+        except api.SbrError as e:
+            if e.status != 5:
+                raise
+            st0 = ctx.launch_stats(probe)
+            cap_r, cap_p = max(cap_r, 2 * st0["records"]), max(cap_p, 2 * st0["paths"])
+        finally:
+            probe.close()
     paths = ctx.paths_create(max(2 * st0["records"], 1024), max(2 * st0["paths"], 256))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -214,12 +238,12 @@ def run_gpu(args):
     def relaunch():
         ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha)
 
-    tuned = autotune.tune_batch_refine(ctx, scene, paths, relaunch, iters, K)
+    tuned = autotune.tune_batch_refine(ctx, scene, paths, relaunch, iters, K, target=target)
     shape = {k: tuned[k] for k in ("block_threads", "lanes_per_path", "blocks_per_sm")}
 
     def step():
         ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha)
-        ctx.batch_refine(scene, paths, iters, K, **shape)
+        ctx.batch_refine(scene, paths, iters, K, target=target, **shape)
 
     # one timed (event) launch to split the step into kernels
     for _ in range(2):
@@ -227,7 +251,7 @@ def run_gpu(args):
     ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, timing=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    ctx.batch_refine(scene, paths, iters, K, **shape)
+    ctx.batch_refine(scene, paths, iters, K, target=target, **shape)
     e1.record(stream)
     torch.cuda.synchronize()
     st_t = ctx.launch_stats(paths)
@@ -276,15 +300,16 @@ def run_gpu(args):
     traffic, traffic_rec = trace_traffic()
 
     # the batched graph form vs the plain per-pair launch-and-refine form
-    per_pair_ms = _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, len(rx))
-    batch_ms = _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream, shape)
+    per_pair_ms = _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, len(tx), len(rx), target)
+    batch_ms = _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream, shape, target)
 
-    e2e = _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape)
+    e2e = _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape, target)
 
     out = {"metric": METRIC, "value": value, "unit": "ray-bounces/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32 (f64 in final refinement iterations)", "data": "synthetic",
-           "config": dict(WORKLOAD, triangles=int(sc.nt), rays=int(10 * n * n + 2), l2="flushed (256 MiB write) "
+           "config": dict({k: v for k, v in W.items() if k != "gen"}, triangles=int(sc.nt), ntx=int(len(tx)),
+                          nrx=int(len(rx)), rays=int(len(tx) * (10 * n * n + 2)), l2="flushed (256 MiB write) "
                           "between timed steps, outside the event-timed region", parallelism="replicas" if world > 1
                           else "single GPU"),
            "refined_paths_per_s": good * args.steps / secs,
@@ -302,7 +327,7 @@ def run_gpu(args):
                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} MEASURED_PEAKS.json)",
                         "flops_per_launch": flops},
            "clocks": clocks, "gpu_launches": 6 * args.steps, "wall_s": t_wall, "e2e": e2e}
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.workload == "canyon":
         stride = 4
         s, g, dt, nr, cores = cpu_oracle_sample(sc, tx, rx, stride)
         out["cpu_baseline"] = {"value": s / dt, "unit": "ray-bounces/s", "cores": cores, "kind": "oracle",
@@ -315,6 +340,80 @@ def run_gpu(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_grad(args):
+    """Gradient workload: 1M fixed face-sequence paths (orders 1-6 from the canyon's refined
+    paths, Tx/Rx jittered by +-1 m); one step = unfolding forward + adjoint (vector-Jacobian
+    product) through the autograd Function.  HBM bound: per path 68 B read (Tx, Rx, az/el,
+    order, 8 face ids) + 32 B written forward, 100 B read (+ the output gradient) + 32 B
+    written (three input gradients) backward; the face-plane table stays in L2."""
+    import torch
+
+    from paper_2208_10009_gb300 import api, scenes
+    from paper_2208_10009_gb300.autograd import unfold
+    dev = torch.device("cuda", 0)
+    sc, tx, rx = scenes.urban_canyon()
+    ctx = api.Context(0)
+    scene = ctx.scene_from(sc)
+    rxs = ctx.rx_upload(rx)
+    paths = ctx.paths_create(1 << 16, 1 << 14)
+    ctx.launch(scene, tx, rxs, paths, 700, 6, rx_angle_scale=float(np.sqrt(3.0)), sync=True)
+    ctx.batch_refine(scene, paths, 6, 9)
+    got = ctx.query(paths)
+    base = got[(got["valid"] == 1) & (got["order"] >= 1)]
+    P = 1 << 20
+    rng = np.random.default_rng(4)
+    b = base[rng.integers(0, len(base), P)]
+    T = torch.tensor(scenes.jitter(rng, tx[b["tx"]], 1.0), dtype=torch.float32, device=dev, requires_grad=True)
+    R = torch.tensor(scenes.jitter(rng, rx[b["rx"]], 1.0), dtype=torch.float32, device=dev, requires_grad=True)
+    d = b["dir"]
+    AE = torch.tensor(np.stack([np.arctan2(d[:, 1], d[:, 0]), np.arctan2(d[:, 2], np.hypot(d[:, 0], d[:, 1]))], -1),
+                      dtype=torch.float32, device=dev, requires_grad=True)
+    F = torch.tensor(b["faces"], dtype=torch.int32, device=dev)
+    O = torch.tensor(b["order"], dtype=torch.int32, device=dev)
+    G = torch.randn((P, 8), device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        T.grad = R.grad = AE.grad = None
+        out = unfold(ctx, scene, T, R, AE, F, O)
+        out.backward(G)
+
+    for _ in range(args.warmup):
+        step()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for a, e in evs:
+        flush.zero_()
+        a.record()
+        step()
+        e.record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(e) for a, e in evs) / args.steps
+    # kernel-only timing of the adjoint (the HBM-bound kernel)
+    out = torch.empty((P, 8), device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.zero_()
+    e0.record()
+    ctx.unfold_bwd(scene, T.detach(), R.detach(), AE.detach(), F, O, G)
+    e1.record()
+    torch.cuda.synchronize()
+    bwd_ms = e0.elapsed_time(e1)
+    peaks, src = _peaks()
+    bwd_bytes = P * (100 + 32)
+    print(json.dumps({"metric": "unfolding forward + adjoint paths/s", "value": P / (ms / 1e3), "unit": "paths/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                      "data": "synthetic", "config": {"workload": "1M fixed face-sequence paths of orders 1-6 from the "
+                                                                  "urban canyon, Tx/Rx jittered +-1 m", "paths": P},
+                      "roofline": {"bound": "hbm", "kernel": "unfold_bwd_kernel", "achieved": bwd_bytes / (bwd_ms / 1e3) / 1e9,
+                                   "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                                   "frac": bwd_bytes / (bwd_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                                   "traffic": None, "peak_source": src, "bwd_ms": bwd_ms}}), flush=True)
+    for h in (paths, rxs, scene):
+        h.close()
+    ctx.close()
 
 
 def _count_accurate(ctx, scene, tx, rx, recs):
@@ -342,31 +441,32 @@ def _count_accurate(ctx, scene, tx, rx, recs):
     return int(ok.sum())
 
 
-def _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, nrx, trials=3):
+def _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, ntx, nrx, target, trials=3):
     """The plain per-pair form: one refinement launch per (Tx, Rx) pair from the host,
     each on the same fresh rough paths as the batched form."""
     import torch
     ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
-    ctx.refine_pair(scene, paths, 0, 0, iters, K)   # builds the per-pair buckets
+    ctx.refine_pair(scene, paths, 0, 0, iters, K, target=target)   # builds the per-pair buckets
     out = []
-    for _ in range(trials):
+    for _ in range(trials if ntx * nrx <= 1024 else 1):
         ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
         t = time.perf_counter()
-        for r in range(nrx):
-            ctx.refine_pair(scene, paths, 0, r, iters, K)
+        for tt in range(ntx):
+            for r in range(nrx):
+                ctx.refine_pair(scene, paths, tt, r, iters, K, target=target)
         torch.cuda.synchronize()
         out.append(1e3 * (time.perf_counter() - t))
     return float(np.median(out))
 
 
-def _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream, shape, trials=3):
+def _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, stream, shape, target, trials=3):
     """The batched form: one graph-captured persistent refinement launch for all pairs,
     timed on the host like the per-pair form, on fresh rough paths each trial."""
     import torch
     ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
-        ctx.batch_refine(scene, paths, iters, K, **shape)
+        ctx.batch_refine(scene, paths, iters, K, target=target, **shape)
     out = []
     for _ in range(trials):
         ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
@@ -377,7 +477,7 @@ def _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, strea
     return float(np.median(out))
 
 
-def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape):
+def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape, target):
     """Same step through the C ABI with host inputs: Tx/Rx from pinned host memory (the
     receiver BVH is rebuilt from them), results read back to pinned host memory."""
     import torch
@@ -392,7 +492,7 @@ def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape):
         nonlocal nbytes_out
         rxs = ctx.rx_upload(rx_h)
         ctx.launch(scene, tx_h, rxs, paths, n, order, rx_angle_scale=alpha)
-        ctx.batch_refine(scene, paths, iters, K, **shape)
+        ctx.batch_refine(scene, paths, iters, K, target=target, **shape)
         got = ctx.query(paths, out_h)
         nbytes_out = len(got) * 128
         rxs.close()
@@ -415,15 +515,20 @@ def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="canyon", choices=sorted(WORKLOADS) + ["grad"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
+    if args.steps is None:
+        args.steps = {"canyon": 300, "shoebox": 300, "grad": 20}.get(args.workload, 5)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "grad":
+        run_grad(args)
     else:
         run_gpu(args)
 

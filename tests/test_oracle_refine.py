@@ -137,3 +137,41 @@ def test_validity_removes_redundant_paths(oracle_mod):
         else:
             rejected_real += im["valid"]
     assert kept > 200 and rejected_real <= 2
+
+
+def test_convergence_orders_distance_and_power(oracle_mod):
+    """§IV, Figs. 8-9 (AOD, distance and power error against the iteration count).  The
+    refined polyline through the bounce points to the exact Rx is a perturbation of the
+    stationary (Fermat) image-method path, so its length error falls with the square of the
+    AOD error, while the power error (Fresnel reflection on lossy faces plus free space)
+    falls linearly with it; at 60 iterations both sit at the double-precision floor."""
+    sc, tx, rx = scenes.shoebox_config()
+    sc.face_eps = scenes.f32_exact([5.31, 5.31, 5.31, 5.31, 3.66, 5.31])
+    S = oracle_mod.Scene.from_generated(sc)
+    res = oracle_mod.sbr_pipeline(S, tx, rx, 64, 3, np.sqrt(3), 9, 5, refine_paths=False)
+    tl = oracle_mod.theta_launch(64)
+    c0 = 299792458.0
+    slope_d, slope_p = [], []
+    for p in res.paths[1::3]:
+        if p["order"] == 0:
+            continue
+        im = oracle_mod.image_path(S, tx[0], rx[0], p["faces"])
+        R0 = max(tl, p["err"])
+        E, D, P = [], [], []
+        for i in (0, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 22, 24, 60):
+            r = oracle_mod.refine(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 6, i)
+            ev = oracle_mod.path_eval(S, tx[0], rx[0], p["faces"], r["dir"])
+            e = _ang(r["dir"], im["aod_dir"])
+            d = abs(ev["delay"] - im["delay"]) * c0
+            pw = abs(ev["power"] - im["power"])
+            if i == 60:
+                assert e < 1e-13 and d < 1e-9 and pw < 1e-9, (p["faces"], e, d, pw)
+            elif 1e-7 < e < 1e-2:
+                E.append(e)
+                D.append(d)
+                P.append(pw)
+        slope_d.append(np.polyfit(np.log(E), np.log(D), 1)[0])
+        slope_p.append(np.polyfit(np.log(E), np.log(P), 1)[0])
+    assert len(slope_d) >= 15
+    assert np.all(np.abs(np.array(slope_d) - 2.0) < 0.05), slope_d
+    assert abs(np.median(slope_p) - 1.0) < 0.1 and np.all(np.abs(np.array(slope_p) - 1.0) < 0.3), slope_p
