@@ -9,7 +9,9 @@ seeded scene generator, which holds none of the method's arithmetic.
 
 Parity status: every function is pinned by the tests under ``tests/`` except the power
 term of :func:`path_eval`, whose formula the paper does not give (parity unpinned
-beyond the single-plane closed form).
+beyond the single-plane closed form), and the power term of :func:`wedge_eval` /
+:func:`wedge_image` (free-space loss only: the paper gives no diffraction coefficient;
+parity unpinned).
 """
 from __future__ import annotations
 
@@ -85,6 +87,16 @@ def _load():
             "ora_unfold": (None, [_vp, ctypes.c_int, _i32, _d, _d, ctypes.c_double, ctypes.c_double, _d, _d]),
             "ora_num_threads": (ctypes.c_int, []),
             "ora_equidistant": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, _d]),
+            "ora_wedges": (ctypes.c_int32, [_vp, _d, _i32]),
+            "ora_wedge_exterior": (ctypes.c_int32, [_vp, ctypes.c_int32, _d]),
+            "ora_diffract": (ctypes.c_int64, [_vp, _d, _d, _i64, ctypes.c_int64, _d, ctypes.c_int32,
+                                              ctypes.c_double, ctypes.c_int64, _i32, _i64, _i32, _d, _d]),
+            "ora_refine_wedge": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int32, _d, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_double, _d, _d, _i32, _d]),
+            "ora_wedge_eval": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int32, _d, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, _d, _i32, _d, _d, _d, _d, _d]),
+            "ora_wedge_image": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                               _d, _d, _d, _d, _d, _d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -365,6 +377,117 @@ def az_el(v):
     return np.arctan2(v[..., 1], v[..., 0]), np.arctan2(v[..., 2], np.hypot(v[..., 0], v[..., 1]))
 
 
+# ----------------------------------------------------------------------------- diffraction
+def wedges(scene: Scene):
+    """Wedges of the scene (see ``wedges_build``): endpoints (W, 2, 3) and face pairs (W, 2)."""
+    lib = _load()
+    n = lib.ora_wedges(scene.handle, None, None)
+    ab = np.zeros((max(n, 1), 6))
+    fc = np.zeros((max(n, 1), 2), np.int32)
+    lib.ora_wedges(scene.handle, _p(ab), _p(fc, _i32))
+    return ab[:n].reshape(-1, 2, 3), fc[:n]
+
+
+def wedge_exterior(scene: Scene, w: int, p) -> bool:
+    return bool(_load().ora_wedge_exterior(scene.handle, int(w), _p(_f64(p, (3,)))))
+
+
+@dataclass
+class DiffractResult:
+    rec_rx: np.ndarray
+    rec_ray: np.ndarray
+    rec_wedge: np.ndarray
+    rec_err: np.ndarray
+    rec_dray: np.ndarray
+
+
+def diffract(scene: Scene, tx, dirs, rx, cone: float, ray_ids=None, cap=None) -> DiffractResult:
+    """Brute-force rough order-1 diffraction search from one Tx (see ``ora_diffract``);
+    records sorted by (ray, wedge, rx)."""
+    lib = _load()
+    tx = _f64(tx, (3,))
+    dirs = _f64(dirs, (-1, 3))
+    rx = _f64(rx, (-1, 3))
+    ids = None if ray_ids is None else np.ascontiguousarray(np.asarray(ray_ids, np.int64))
+    cap = cap or max(1024, len(dirs))
+    while True:
+        r_rx = np.zeros(cap, np.int32)
+        r_ray = np.zeros(cap, np.int64)
+        r_w = np.zeros(cap, np.int32)
+        r_err = np.zeros(cap)
+        r_dr = np.zeros(cap)
+        cnt = lib.ora_diffract(scene.handle, _p(tx), _p(dirs), _p(ids, _i64), len(dirs), _p(rx), len(rx), cone, cap,
+                               _p(r_rx, _i32), _p(r_ray, _i64), _p(r_w, _i32), _p(r_err), _p(r_dr))
+        if cnt <= cap:
+            break
+        cap = int(cnt) + 16
+    c = int(cnt)
+    o = np.lexsort((r_rx[:c], r_w[:c], r_ray[:c]))
+    return DiffractResult(r_rx[:c][o], r_ray[:c][o], r_w[:c][o], r_err[:c][o], r_dr[:c][o])
+
+
+def dedup_wedge(dr: DiffractResult, tx_id: int = 0):
+    """Double-count removal for diffraction records: one path per (Tx, Rx, wedge), the
+    smallest error angle, ties to the lowest ray id."""
+    best = {}
+    for i in range(len(dr.rec_err)):
+        key = (tx_id, int(dr.rec_rx[i]), int(dr.rec_wedge[i]))
+        cand = (float(dr.rec_err[i]), int(dr.rec_ray[i]), float(dr.rec_dray[i]))
+        if key not in best or cand[:2] < best[key][:2]:
+            best[key] = cand
+    return [dict(tx=k[0], rx=k[1], wedge=k[2], order=1, faces=(-1 - k[2],), err=v[0], ray=v[1], dray=v[2],
+                 diffraction=True) for k, v in sorted(best.items())]
+
+
+def refine_wedge(scene: Scene, tx, rx, w: int, c0, R0: float, K: int, iters: int, target: float = 0.0):
+    """The precise algorithm for a diffraction path (see ``ora_refine_wedge``)."""
+    out_dir = np.zeros(3)
+    out_err = np.zeros(1)
+    choice = np.full(max(iters, 1), -1, np.int32)
+    hist = np.full(iters + 1, np.nan)
+    it = _load().ora_refine_wedge(scene.handle, _p(_f64(tx, (3,))), _p(_f64(rx, (3,))), int(w),
+                                  _p(_f64(c0, (3,))), R0, K, iters, target, _p(out_dir), _p(out_err),
+                                  _p(choice, _i32), _p(hist))
+    if it < 0:
+        raise ValueError("bad sub-ray count or Tx on the edge line")
+    return dict(dir=out_dir, err=float(out_err[0]), iters=it, choice=choice[:it], err_hist=hist[: it + 1])
+
+
+def wedge_eval(scene: Scene, tx, rx, w: int, direction, freq=2.4e9, ptx_dbm=0.0, err_bound=0.0):
+    """Validity test and outputs of a diffraction path (see ``ora_wedge_eval``)."""
+    q = np.zeros(3)
+    valid = np.zeros(1, np.int32)
+    delay, power, err = np.zeros(1), np.zeros(1), np.zeros(1)
+    aod, aoa = np.zeros(2), np.zeros(2)
+    r = _load().ora_wedge_eval(scene.handle, _p(_f64(tx, (3,))), _p(_f64(rx, (3,))), int(w),
+                               _p(_f64(direction, (3,))), freq, ptx_dbm, err_bound, _p(q), _p(valid, _i32),
+                               _p(delay), _p(aod), _p(aoa), _p(power), _p(err))
+    return dict(ok=(r == 0), valid=bool(valid[0]), point=q, delay=float(delay[0]), aod=aod, aoa=aoa,
+                power=float(power[0]), err=float(err[0]))
+
+
+def wedge_image(scene: Scene, tx, rx, w: int, freq=2.4e9, ptx_dbm=0.0):
+    """Exact order-1 diffraction path at wedge w (see ``ora_wedge_image``)."""
+    q, d = np.zeros(3), np.zeros(3)
+    delay, power = np.zeros(1), np.zeros(1)
+    aod, aoa = np.zeros(2), np.zeros(2)
+    r = _load().ora_wedge_image(scene.handle, _p(_f64(tx, (3,))), _p(_f64(rx, (3,))), int(w), freq, ptx_dbm,
+                                _p(q), _p(d), _p(delay), _p(aod), _p(aoa), _p(power))
+    return dict(status=r, valid=(r == 1), point=q, aod_dir=d, delay=float(delay[0]), aod=aod, aoa=aoa,
+                power=float(power[0]))
+
+
+def wedge_enumerate(scene: Scene, tx, rx):
+    """Every valid exact order-1 diffraction path from tx to rx: {wedge: wedge_image dict}."""
+    nw = len(wedges(scene)[1])
+    out = {}
+    for w in range(nw):
+        r = wedge_image(scene, tx, rx, w)
+        if r["valid"]:
+            out[w] = r
+    return out
+
+
 # ----------------------------------------------------------------------------- pipeline
 @dataclass
 class PipelineResult:
@@ -377,14 +500,15 @@ class PipelineResult:
 
 def sbr_pipeline(scene: Scene, txs, rxs, n: int, max_order: int, alpha: float, K: int, iters: int,
                  target: float = 0.0, ray_ids=None, want_margin=False, freq=2.4e9, keep_traces=False,
-                 refine_paths=True, launcher: int = 0):
+                 refine_paths=True, launcher: int = 0, diffraction: bool = False):
     """The whole hot path in the paper's order (Fig. 4): equiangular launch, brute-force
     trace with reception, double-count removal, the precise algorithm, then the validity
     test and outputs.  The reception cone is alpha * theta_launch; the precise algorithm's
     initial cone is the ray cone of Eq. 8, theta_launch, widened to the rough error angle
     when that is larger (alpha > 1 can accept a ray outside its own cone), so the exact
     direction is always inside it.  ``ray_ids`` restricts the launch to a subsample of the
-    lattice."""
+    lattice.  ``diffraction`` adds the order-1 diffraction paths (one per Tx, Rx, wedge)
+    after each Tx's reflection paths."""
     txs = _f64(txs, (-1, 3))
     rxs = _f64(rxs, (-1, 3))
     cone = alpha * theta_launch(n)
@@ -415,5 +539,22 @@ def sbr_pipeline(scene: Scene, txs, rxs, n: int, max_order: int, alpha: float, K
                 ev = path_eval(scene, tx, rxs[p["rx"]], p["faces"], r["dir"], freq, err_bound=bound)
                 p.update(valid=ev["valid"], delay=ev["delay"], aod=ev["aod"], aoa=ev["aoa"], power=ev["power"],
                          points=ev["points"])
+            paths.append(p)
+        if not diffraction:
+            continue
+        dr = diffract(scene, tx, dirs, rxs, cone, ray_ids=ids)
+        nrec += len(dr.rec_err)
+        for p in dedup_wedge(dr, t):
+            c0 = lattice_ids(n, [p["ray"]])[0] if not launcher else all_dirs[p["ray"]]
+            p["rough_dir"] = c0
+            if refine_paths:
+                R0 = max(theta_launch(n), p["err"])
+                r = refine_wedge(scene, tx, rxs[p["rx"]], p["wedge"], c0, R0, K, iters, target)
+                p.update(ref_dir=r["dir"], ref_err=r["err"], iters=r["iters"], choice=r["choice"],
+                         err_hist=r["err_hist"])
+                bound = refined_err_bound(R0, K, r["iters"]) if r["iters"] > 0 else 0.0
+                ev = wedge_eval(scene, tx, rxs[p["rx"]], p["wedge"], r["dir"], freq, err_bound=bound)
+                p.update(valid=ev["valid"], delay=ev["delay"], aod=ev["aod"], aoa=ev["aoa"], power=ev["power"],
+                         points=ev["point"][None, :])
             paths.append(p)
     return PipelineResult(paths, nseg, len(dirs) * len(txs), nrec, traces)

@@ -18,6 +18,9 @@
  *   unfolding gradients: pinned by tests (closed forms, brute force, invariants).
  *   ora_path_eval power term: parity unpinned beyond the single-plane closed form
  *   (the paper gives no power formula; the Fresnel/free-space reading is ours).
+ *   Order-1 diffraction (wedges, rough search, refinement, validity, outputs, exact
+ *   diffraction point): pinned by tests; its power term is free-space loss only (the paper
+ *   gives no diffraction coefficient): parity unpinned.
  */
 #include <math.h>
 #include <stdint.h>
@@ -413,6 +416,8 @@ typedef struct {
     double *eps;      /* relative permittivity per face (<= 0: perfect reflector) */
     unsigned char *boundary; /* 3 flags per triangle: edge (v_i, v_i+1) bounds its face */
     double scale;     /* bounding-box diagonal */
+    struct wedge_s *wd;      /* wedges (diffraction), built on first use */
+    int nw, wedges_built;
 } scene;
 
 typedef struct { int a, b, face; int64_t tri; int slot; } edge_rec;
@@ -485,6 +490,7 @@ void ora_scene_free(void *p) {
     scene *s = (scene *)p;
     if (!s) return;
     free(s->V); free(s->T); free(s->tf); free(s->fn); free(s->fh); free(s->eps); free(s->boundary);
+    free(s->wd);
     free(s);
 }
 
@@ -1097,4 +1103,393 @@ int ora_num_threads(void) {
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* order-1 diffraction: §III.A (Fig. 4, both path tests name faces and       */
+/* wedges), §III.B last paragraph, §IV (Figs. 7c-d and 8b)                   */
+/* ------------------------------------------------------------------------- */
+/*
+ * Wedges.  The paper diffracts rays at the wedges of its scenes without defining one; the
+ * reading taken here: a wedge is a side shared by two faces -- the same segment, with
+ * identical endpoint coordinates, on the boundary of both -- whose half-planes meet at an
+ * interior angle between 1 and 170 degrees.  A face's sides are its boundary triangle
+ * edges with collinear neighbours (sharing a vertex) merged.  The solid fills the smaller
+ * of the two sectors the half-planes bound; the larger one (> pi) is the exterior, where
+ * both ends of a diffracted path must lie.  Wedge ids follow the order of the face pairs
+ * (f1 < f2).  w1, w2 are the unit vectors perpendicular to the edge pointing into face f1
+ * and f2 (towards the mean of the face's triangle vertices).
+ */
+typedef struct wedge_s {
+    vec3 a, b, e, w1, w2;
+    int f1, f2;
+} wedge_t;
+
+typedef struct { vec3 pa, pb; int ia, ib, face, alive; } side_t;
+typedef struct { double k[6]; int face; vec3 a, b; } side_key;
+
+static int side_key_cmp(const void *x, const void *y) {
+    const side_key *p = (const side_key *)x, *q = (const side_key *)y;
+    for (int i = 0; i < 6; ++i)
+        if (p->k[i] != q->k[i]) return p->k[i] < q->k[i] ? -1 : 1;
+    return p->face < q->face ? -1 : (p->face > q->face ? 1 : 0);
+}
+
+static int lex_less(vec3 a, vec3 b) {
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return a.z < b.z;
+}
+
+static int wedge_cmp(const void *x, const void *y) {
+    const wedge_t *p = (const wedge_t *)x, *q = (const wedge_t *)y;
+    if (p->f1 != q->f1) return p->f1 < q->f1 ? -1 : 1;
+    return p->f2 < q->f2 ? -1 : (p->f2 > q->f2 ? 1 : 0);
+}
+
+static vec3 perp_to(vec3 v, vec3 e) { return sub(v, scl(e, dot(v, e))); }
+
+static void wedges_build(scene *s) {
+    if (s->wedges_built) return;
+    s->wedges_built = 1;
+    /* boundary edges grouped by face */
+    int64_t nb = 0;
+    for (int64_t t = 0; t < s->nt; ++t)
+        for (int k = 0; k < 3; ++k) nb += s->boundary[3 * t + k];
+    side_t *sd = (side_t *)malloc(sizeof(side_t) * (nb > 0 ? nb : 1));
+    int64_t *start = (int64_t *)calloc((size_t)s->nf + 1, sizeof(int64_t));
+    for (int64_t t = 0; t < s->nt; ++t)
+        for (int k = 0; k < 3; ++k)
+            if (s->boundary[3 * t + k]) ++start[s->tf[t] + 1];
+    for (int f = 0; f < s->nf; ++f) start[f + 1] += start[f];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * ((size_t)s->nf + 1));
+    memcpy(fill, start, sizeof(int64_t) * ((size_t)s->nf + 1));
+    vec3 *cen = (vec3 *)calloc((size_t)s->nf + 1, sizeof(vec3));
+    double *cnt = (double *)calloc((size_t)s->nf + 1, sizeof(double));
+    for (int64_t t = 0; t < s->nt; ++t) {
+        int f = s->tf[t];
+        for (int k = 0; k < 3; ++k) {
+            cen[f] = add(cen[f], s->V[s->T[3 * t + k]]);
+            cnt[f] += 1.0;
+            if (!s->boundary[3 * t + k]) continue;
+            side_t e;
+            e.ia = s->T[3 * t + k];
+            e.ib = s->T[3 * t + (k + 1) % 3];
+            e.pa = s->V[e.ia];
+            e.pb = s->V[e.ib];
+            e.face = f;
+            e.alive = 1;
+            sd[fill[f]++] = e;
+        }
+    }
+    for (int f = 0; f < s->nf; ++f)
+        if (cnt[f] > 0) cen[f] = scl(cen[f], 1.0 / cnt[f]);
+    /* merge collinear boundary edges of each face that share a vertex */
+    for (int f = 0; f < s->nf; ++f) {
+        int merged = 1;
+        while (merged) {
+            merged = 0;
+            for (int64_t i = start[f]; i < start[f + 1]; ++i) {
+                if (!sd[i].alive) continue;
+                for (int64_t j = start[f]; j < start[f + 1]; ++j) {
+                    if (j == i || !sd[j].alive) continue;
+                    side_t *p = &sd[i], *q = &sd[j];
+                    int shared, pfar, qfar;
+                    vec3 pf, qf;
+                    if (p->ib == q->ia) { shared = 1; pf = p->pa; pfar = p->ia; qf = q->pb; qfar = q->ib; }
+                    else if (p->ib == q->ib) { shared = 1; pf = p->pa; pfar = p->ia; qf = q->pa; qfar = q->ia; }
+                    else if (p->ia == q->ia) { shared = 1; pf = p->pb; pfar = p->ib; qf = q->pb; qfar = q->ib; }
+                    else if (p->ia == q->ib) { shared = 1; pf = p->pb; pfar = p->ib; qf = q->pa; qfar = q->ia; }
+                    else shared = 0;
+                    if (!shared) continue;
+                    vec3 d1 = sub(p->pb, p->pa), d2 = sub(q->pb, q->pa);
+                    if (norm(cross(d1, d2)) > 1e-6 * norm(d1) * norm(d2)) continue;
+                    p->pa = pf; p->ia = pfar;
+                    p->pb = qf; p->ib = qfar;
+                    q->alive = 0;
+                    merged = 1;
+                }
+            }
+        }
+    }
+    /* sides shared by exactly two faces */
+    side_key *keys = (side_key *)malloc(sizeof(side_key) * (nb > 0 ? nb : 1));
+    int64_t nk = 0;
+    for (int64_t i = 0; i < nb; ++i) {
+        if (!sd[i].alive) continue;
+        vec3 lo = sd[i].pa, hi = sd[i].pb;
+        if (lex_less(hi, lo)) { vec3 tmp = lo; lo = hi; hi = tmp; }
+        side_key k;
+        k.k[0] = lo.x; k.k[1] = lo.y; k.k[2] = lo.z; k.k[3] = hi.x; k.k[4] = hi.y; k.k[5] = hi.z;
+        k.face = sd[i].face;
+        k.a = lo;
+        k.b = hi;
+        keys[nk++] = k;
+    }
+    qsort(keys, (size_t)nk, sizeof(side_key), side_key_cmp);
+    wedge_t *W = (wedge_t *)malloc(sizeof(wedge_t) * (nk > 0 ? nk : 1));
+    int nw = 0;
+    for (int64_t i = 0; i < nk;) {
+        int64_t j = i;
+        while (j < nk && memcmp(keys[j].k, keys[i].k, sizeof(keys[i].k)) == 0) ++j;
+        if (j - i == 2 && keys[i].face != keys[i + 1].face) {
+            wedge_t w;
+            w.a = keys[i].a;
+            w.b = keys[i].b;
+            w.e = unit(sub(w.b, w.a));
+            w.f1 = keys[i].face;
+            w.f2 = keys[i + 1].face;
+            w.w1 = unit(perp_to(sub(cen[w.f1], w.a), w.e));
+            w.w2 = unit(perp_to(sub(cen[w.f2], w.a), w.e));
+            double phi = angle_between(w.w1, w.w2) * 180.0 / M_PI;
+            if (phi >= 1.0 && phi <= 170.0) W[nw++] = w;
+        }
+        i = j;
+    }
+    qsort(W, (size_t)nw, sizeof(wedge_t), wedge_cmp);
+    s->wd = W;
+    s->nw = nw;
+    free(keys); free(sd); free(start); free(fill); free(cen); free(cnt);
+}
+
+/* Number of wedges; writes (a, b) as 6 doubles and (f1, f2) per wedge when non-null. */
+int32_t ora_wedges(void *sp, double *ab, int32_t *faces) {
+    scene *s = (scene *)sp;
+    wedges_build(s);
+    for (int i = 0; i < s->nw; ++i) {
+        if (ab) { st(ab + 6 * i, s->wd[i].a); st(ab + 6 * i + 3, s->wd[i].b); }
+        if (faces) { faces[2 * i] = s->wd[i].f1; faces[2 * i + 1] = s->wd[i].f2; }
+    }
+    return s->nw;
+}
+
+/* p lies in the wedge's exterior: not strictly inside the interior sector of w1, w2 */
+static int wedge_exterior(const wedge_t *w, vec3 p) {
+    vec3 q = perp_to(sub(p, w->a), w->e);
+    vec3 nrm = cross(w->w1, w->w2);
+    int inside = dot(cross(w->w1, q), nrm) > 0.0 && dot(cross(q, w->w2), nrm) > 0.0;
+    return !inside;
+}
+
+int32_t ora_wedge_exterior(void *sp, int32_t wi, const double *p3) {
+    scene *s = (scene *)sp;
+    wedges_build(s);
+    return wedge_exterior(&s->wd[wi], ld(p3));
+}
+
+/*
+ * Unfolding across the edge line (the diffraction analogue of mirroring through a face
+ * plane): Rx rotated about the edge line into the half-plane through the edge that is
+ * opposite Tx.  Rotation about the edge keeps the angle to the edge, so a ray from Tx
+ * that crosses the edge line and continues straight towards the image Rx* is, once
+ * folded back, a ray on the Keller cone of diffraction (§III.B: the sub-rays diffract
+ * along the recorded direction; the azimuth around the cone that reaches the receiver
+ * is the limit of the rays sent to both sides of it).  Eq. 3's error angle of a launch
+ * direction d is then angle(d, Rx* - Tx), and the exact diffraction point is where the
+ * segment Tx -> Rx* crosses the edge line.  Returns 0 if Tx lies on the edge line.
+ */
+static int wedge_unfold_rx(const wedge_t *w, vec3 tx, vec3 rx, vec3 *out) {
+    vec3 qt = sub(tx, w->a), qr = sub(rx, w->a);
+    vec3 pt = perp_to(qt, w->e), pr = perp_to(qr, w->e);
+    double rt = norm(pt), rr = norm(pr);
+    if (!(rt > 0.0)) return 0;
+    *out = add(w->a, sub(scl(w->e, dot(qr, w->e)), scl(pt, rr / rt)));
+    return 1;
+}
+
+/* point of the edge segment seen from o at the smallest angle to d; returns that angle */
+static double wedge_nearest_seen(const wedge_t *w, vec3 o, vec3 d, vec3 *x_out) {
+    vec3 a0 = sub(w->a, o), eb = sub(w->b, w->a);
+    double al = dot(d, a0), be = dot(d, eb), c = dot(a0, a0), ep = dot(a0, eb), g = dot(eb, eb);
+    double cand[3] = {0.0, 1.0, -1.0};
+    double den = be * ep - al * g;
+    if (den != 0.0) {
+        double u = (al * ep - be * c) / den;
+        if (u > 0.0 && u < 1.0) cand[2] = u;
+    }
+    double best = INFINITY;
+    for (int i = 0; i < 3; ++i) {
+        if (cand[i] < 0.0) continue;
+        vec3 v = add(a0, scl(eb, cand[i]));
+        double ang = angle_between(d, v);
+        if (ang < best) { best = ang; *x_out = add(o, v); }
+    }
+    return best;
+}
+
+/*
+ * Rough order-1 diffraction search (§III.A, Fig. 4) for the rays of one Tx.  A ray's
+ * first segment (from Tx to its first hit at t0, or to infinity) meets wedge w when the
+ * edge point X seen at the smallest angle to the ray lies inside the ray cone (angle <=
+ * cone) and not behind the first hit (foot s_X in (0, t0 (1 + tan cone)]), and Tx lies in
+ * the wedge's exterior.  The diffracted rays leave X on its Keller cone; receiver r
+ * receives one when it lies in the exterior, its error angle of Eq. 3 in the unfolded
+ * space, angle(d, Rx* - Tx), is <= cone, and the segment X -> Rx is not blocked (the
+ * wedge's two faces excluded).  Each such (ray, wedge, rx) is a record: error angle and
+ * d_ray = |Rx* - Tx| cos(error).  Returns the record count (first `cap` written).
+ */
+int64_t ora_diffract(void *sp, const double *tx3, const double *dirs, const int64_t *ray_ids, int64_t nrays,
+                     const double *rx, int32_t nrx, double cone, int64_t cap, int32_t *rec_rx, int64_t *rec_ray,
+                     int32_t *rec_wedge, double *rec_err, double *rec_dray) {
+    scene *s = (scene *)sp;
+    wedges_build(s);
+    vec3 tx = ld(tx3);
+    int64_t nrec = 0;
+    double tmin = 1e-7 * s->scale, tc = tan(cone);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < nrays; ++i) {
+        vec3 d = ld(dirs + 3 * i);
+        double t0;
+        int64_t hit = closest_hit(s, tx, d, -1, tmin, &t0);
+        double gate = hit >= 0 ? t0 * (1.0 + tc) : INFINITY;
+        for (int wi = 0; wi < s->nw; ++wi) {
+            const wedge_t *w = &s->wd[wi];
+            vec3 X;
+            double ang = wedge_nearest_seen(w, tx, d, &X);
+            if (!(ang <= cone)) continue;
+            double sx = dot(sub(X, tx), d);
+            if (!(sx > 0.0 && sx <= gate)) continue;
+            if (!wedge_exterior(w, tx)) continue;
+            for (int r = 0; r < nrx; ++r) {
+                vec3 R = ld(rx + 3 * r), Rs;
+                if (!wedge_exterior(w, R) || !wedge_unfold_rx(w, tx, R, &Rs)) continue;
+                vec3 W = sub(Rs, tx);
+                double err = angle_between(d, W);
+                if (!(err <= cone)) continue;
+                if (occluded(s, X, R, w->f1, w->f2)) continue;
+                int64_t slot;
+#pragma omp atomic capture
+                slot = nrec++;
+                if (slot < cap) {
+                    rec_rx[slot] = r;
+                    rec_ray[slot] = ray_ids ? ray_ids[i] : i;
+                    rec_wedge[slot] = wi;
+                    rec_err[slot] = err;
+                    rec_dray[slot] = norm(W) * cos(err);
+                }
+            }
+        }
+    }
+    return nrec;
+}
+
+/*
+ * The precise algorithm (§III.B, Fig. 5, Eq. 10) for a diffraction path at wedge wi: the
+ * same sub-ray pattern, argmin and shrink as ora_refine, with Eq. 3 evaluated in the
+ * unfolded space of the wedge (see wedge_unfold_rx): error(d) = angle(d, Rx* - Tx) for
+ * d . (Rx* - Tx) > 0, else +inf.  Returns iterations done (-1 for a bad K or Tx on the
+ * edge line).
+ */
+int ora_refine_wedge(void *sp, const double *tx3, const double *rx3, int32_t wi, const double *c0, double R0,
+                     int K, int iters, double target, double *out_dir, double *out_err, int32_t *choice,
+                     double *err_hist) {
+    scene *s = (scene *)sp;
+    wedges_build(s);
+    double rho[16], phi[16], shrink;
+    if (ora_subray_pattern(K, rho, phi, &shrink) != K) return -1;
+    vec3 tx = ld(tx3), rx = ld(rx3), c = unit(ld(c0)), Rs;
+    if (!wedge_unfold_rx(&s->wd[wi], tx, rx, &Rs)) return -1;
+    vec3 W = sub(Rs, tx);
+    double R = R0;
+    double err = dot(c, W) > 0.0 ? angle_between(c, W) : INFINITY;
+    if (err_hist) err_hist[0] = err;
+    int it = 0;
+    while (it < iters && !(target > 0 && err <= target)) {
+        vec3 u, v, best_d = c;
+        double best = INFINITY;
+        int bk = -1;
+        cone_frame(c, &u, &v);
+        for (int k = 0; k < K; ++k) {
+            double a = rho[k] * R;
+            vec3 dk = add(scl(c, cos(a)), scl(add(scl(u, cos(phi[k])), scl(v, sin(phi[k]))), sin(a)));
+            double e = dot(dk, W) > 0.0 ? angle_between(dk, W) : INFINITY;
+            if (e < best) { best = e; bk = k; best_d = dk; }
+        }
+        if (bk < 0) break;
+        c = best_d;
+        err = best;
+        R *= shrink;
+        if (choice) choice[it] = bk;
+        ++it;
+        if (err_hist) err_hist[it] = err;
+    }
+    st(out_dir, c);
+    *out_err = err;
+    return it;
+}
+
+/*
+ * Validity test and outputs of a diffraction path launched along `dir` (§III.A second
+ * path test: the path must touch its wedge; §IV outputs).  The diffraction point Q is
+ * the point of the edge line closest to the launched ray.  Valid iff Q lies on the edge
+ * segment and ahead of Tx, Tx and Rx lie in the wedge's exterior, Tx -> Q and Q -> Rx are
+ * not blocked (the wedge's faces excluded) and -- when err_bound > 0 -- the error angle
+ * is at most err_bound.  Outputs: delay = (|Q - Tx| + |Rx - Q|) / c0; AOD = dir; AOA =
+ * Q - Rx; power = ptx + free-space loss over the path length (the paper gives no
+ * diffraction coefficient; parity unpinned).  Writes Q to q_out.  Returns 0, or -1 if
+ * Tx lies on the edge line.
+ */
+int ora_wedge_eval(void *sp, const double *tx3, const double *rx3, int32_t wi, const double *dir, double freq,
+                   double ptx_dbm, double err_bound, double *q_out, int32_t *valid, double *delay, double *aod,
+                   double *aoa, double *power, double *err) {
+    scene *s = (scene *)sp;
+    wedges_build(s);
+    const wedge_t *w = &s->wd[wi];
+    vec3 tx = ld(tx3), rx = ld(rx3), d = unit(ld(dir)), Rs;
+    *valid = 0;
+    if (!wedge_unfold_rx(w, tx, rx, &Rs)) return -1;
+    vec3 W = sub(Rs, tx);
+    double e = dot(d, W) > 0.0 ? angle_between(d, W) : INFINITY;
+    *err = e;
+    /* closest points of the lines tx + s d and a + u (b - a) */
+    vec3 eb = sub(w->b, w->a), w0 = sub(tx, w->a);
+    double A = 1.0, B = dot(d, eb), C = dot(eb, eb), D = dot(d, w0), E = dot(eb, w0);
+    double den = A * C - B * B;
+    double u = den != 0.0 ? (A * E - B * D) / den : -1.0;
+    double sq = den != 0.0 ? (B * E - C * D) / den : -1.0;
+    vec3 Q = add(w->a, scl(eb, u));
+    if (q_out) st(q_out, Q);
+    int ok = u >= 0.0 && u <= 1.0 && sq > 0.0 && wedge_exterior(w, tx) && wedge_exterior(w, rx);
+    if (ok && (occluded(s, tx, Q, w->f1, w->f2) || occluded(s, Q, rx, w->f1, w->f2))) ok = 0;
+    if (err_bound > 0.0 && !(e <= err_bound)) ok = 0;
+    *valid = ok;
+    double len = norm(sub(Q, tx)) + norm(sub(rx, Q));
+    *delay = len / ORA_C0;
+    az_el(d, aod);
+    az_el(sub(Q, rx), aoa);
+    *power = ptx_dbm + 20.0 * log10(ORA_C0 / freq / (4.0 * M_PI * len));
+    return 0;
+}
+
+/*
+ * Exact order-1 diffraction path at wedge wi (the image-method counterpart): the point Q*
+ * where Tx -> Rx* crosses the edge line, i.e. along the edge at z_T + (z_R - z_T) r_T /
+ * (r_T + r_R) (z: position along the edge, r: distance from it), the minimum of |Tx - Q| +
+ * |Q - Rx| over the line (Fermat) where Keller's law holds.  Returns 1 if valid (Q* on the
+ * segment, both ends exterior, unblocked), 0 if not, -1 if Tx lies on the edge line.
+ */
+int ora_wedge_image(void *sp, const double *tx3, const double *rx3, int32_t wi, double freq, double ptx_dbm,
+                    double *q_out, double *aod_dir, double *delay, double *aod, double *aoa, double *power) {
+    scene *s = (scene *)sp;
+    wedges_build(s);
+    const wedge_t *w = &s->wd[wi];
+    vec3 tx = ld(tx3), rx = ld(rx3);
+    vec3 qt = sub(tx, w->a), qr = sub(rx, w->a);
+    double zt = dot(qt, w->e), zr = dot(qr, w->e);
+    double rt = norm(perp_to(qt, w->e)), rr = norm(perp_to(qr, w->e));
+    if (!(rt > 0.0)) return -1;
+    double z = zt + (zr - zt) * rt / (rt + rr);
+    vec3 Q = add(w->a, scl(w->e, z));
+    st(q_out, Q);
+    vec3 dir = unit(sub(Q, tx));
+    st(aod_dir, dir);
+    double len = norm(sub(Q, tx)) + norm(sub(rx, Q));
+    *delay = len / ORA_C0;
+    az_el(dir, aod);
+    az_el(sub(Q, rx), aoa);
+    *power = ptx_dbm + 20.0 * log10(ORA_C0 / freq / (4.0 * M_PI * len));
+    double L = norm(sub(w->b, w->a));
+    int ok = z >= 0.0 && z <= L && wedge_exterior(w, tx) && wedge_exterior(w, rx);
+    if (ok && (occluded(s, tx, Q, w->f1, w->f2) || occluded(s, Q, rx, w->f1, w->f2))) ok = 0;
+    return ok;
 }

@@ -1,0 +1,198 @@
+"""Pins for the oracle's order-1 diffraction (§III.A Fig. 4 and both path tests, §III.B last
+paragraph, §IV Figs. 7c-d and 8b): wedge extraction, the exterior sector, the exact
+diffraction point (Fermat / Keller), the unfolded error angle, the precise algorithm and
+the rough SBR search against the exact paths."""
+import numpy as np
+import pytest
+
+from paper_2208_10009_gb300 import scenes
+
+C0 = 299792458.0
+
+
+def _ang(a, b):
+    return np.arctan2(np.linalg.norm(np.cross(a, b)), np.dot(a, b))
+
+
+def _box(lo, hi, g=1, bottom=True):
+    b = scenes._Builder()
+    scenes.box_faces(b, lo, hi, g, bottom=bottom)
+    return b.finish()
+
+
+def test_wedges_of_boxes(oracle_mod):
+    """A closed box has its 12 edges as 90-degree wedges; without the bottom face, 8; a
+    tessellated box gives the same full-length edges; a box standing on a separate ground
+    plane adds none (the ground shares no side with it)."""
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4)))
+    ab, fc = oracle_mod.wedges(S)
+    assert len(fc) == 12
+    assert np.all(fc[:, 0] < fc[:, 1]) and np.all(np.diff(fc[:, 0] * 100 + fc[:, 1]) > 0)
+    lens = sorted(np.round(np.linalg.norm(ab[:, 1] - ab[:, 0], axis=1), 9))
+    assert lens == [2.0] * 4 + [3.0] * 4 + [4.0] * 4
+    corners = {tuple(p) for p in ab.reshape(-1, 3)}
+    assert corners == {(x, y, z) for x in (0, 2) for y in (0, 3) for z in (0, 4)}
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4), bottom=False))
+    assert len(oracle_mod.wedges(S)[1]) == 8
+    S3 = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4), g=3, bottom=False))
+    ab3, fc3 = oracle_mod.wedges(S3)
+    assert len(fc3) == 8
+    assert sorted(np.round(np.linalg.norm(ab3[:, 1] - ab3[:, 0], axis=1), 9)) == [2.0] * 2 + [3.0] * 2 + [4.0] * 4
+    b = scenes._Builder()
+    b.quad((-10, -10, 0), (10, -10, 0), (-10, 10, 0), 4)
+    scenes.box_faces(b, (0, 0, 0), (2, 3, 4), bottom=False)
+    assert len(oracle_mod.wedges(oracle_mod.Scene.from_generated(b.finish()))[1]) == 8
+
+
+def test_wedges_of_tetrahedron_and_flat_faces(oracle_mod):
+    """A regular tetrahedron: 6 wedges (interior angle acos(1/3) = 70.5 deg).  Two coplanar
+    faces side by side share a side but form no wedge; neither does a fold of 175 deg."""
+    v = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float)
+    b = scenes._Builder()
+    for f in ([0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]):
+        b.polygon(v[f])
+    S = oracle_mod.Scene.from_generated(b.finish())
+    assert len(oracle_mod.wedges(S)[1]) == 6
+    b = scenes._Builder()
+    b.quad((0, 0, 0), (1, 0, 0), (0, 1, 0))
+    b.quad((1, 0, 0), (2, 0, 0), (1, 1, 0))
+    a = np.radians(5.0)
+    b.quad((2, 0, 0), (2 + np.cos(a), 0, np.sin(a)), (2, 1, 0))
+    assert len(oracle_mod.wedges(oracle_mod.Scene.from_generated(b.finish()))[1]) == 0
+
+
+def test_exterior_sector(oracle_mod):
+    """For the vertical box edge at x = y = 0 the solid fills the quarter x > 0, y > 0; the
+    other three quarters are the exterior."""
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4)))
+    ab, fc = oracle_mod.wedges(S)
+    w = [i for i in range(len(fc)) if np.allclose(ab[i, :, :2], 0)][0]
+    assert not oracle_mod.wedge_exterior(S, w, [0.5, 0.5, 1.0])
+    for p in ([-1, 0.5, 1], [-1, -1, 3], [0.5, -1, 2], [5, -0.1, 9]):
+        assert oracle_mod.wedge_exterior(S, w, p)
+
+
+def _rotate(p, a, e, ang):
+    """Rodrigues rotation of point p about the axis through a along unit e by ang."""
+    v = p - a
+    return a + v * np.cos(ang) + np.cross(e, v) * np.sin(ang) + e * np.dot(e, v) * (1 - np.cos(ang))
+
+
+def test_exact_diffraction_point_is_fermat_and_keller(oracle_mod):
+    """The exact diffraction point minimises |Tx - Q| + |Q - Rx| over the edge line
+    (checked by a dense scan), the incident and diffracted rays make equal angles with the
+    edge (Keller's law), and the path length equals |Rx* - Tx| for Rx rotated about the
+    edge into the half-plane opposite Tx."""
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (20, 30, 40)))
+    ab, fc = oracle_mod.wedges(S)
+    rng = np.random.default_rng(7)
+    checked = 0
+    for w in range(len(fc)):
+        a, b = ab[w]
+        e = (b - a) / np.linalg.norm(b - a)
+        for _ in range(6):
+            tx = rng.uniform(-30, 60, 3)
+            rx = rng.uniform(-30, 60, 3)
+            r = oracle_mod.wedge_image(S, tx, rx, w)
+            if r["status"] < 0:
+                continue
+            Q = r["point"]
+            z = np.linspace(-200, 200, 40001)
+            L = [np.linalg.norm(tx - (a + e * t)) + np.linalg.norm(rx - (a + e * t)) for t in z]
+            i = int(np.argmin(L))
+            length = r["delay"] * C0
+            assert length <= L[i] + 1e-9
+            assert abs(np.dot(Q - a, e) - z[i]) < 0.02
+            assert abs(np.dot(Q - tx, e) / np.linalg.norm(Q - tx) - np.dot(rx - Q, e) / np.linalg.norm(rx - Q)) < 1e-12
+            # Rx rotated about the edge into the plane of Tx, opposite side
+            pt = (tx - a) - e * np.dot(tx - a, e)
+            pr = (rx - a) - e * np.dot(rx - a, e)
+            ang = np.arctan2(np.dot(np.cross(pr, -pt), e), np.dot(pr, -pt))
+            rs = _rotate(rx, a, e, ang)
+            assert abs(np.linalg.norm(rs - tx) - length) < 1e-9 * length
+            assert _ang(rs - tx, r["aod_dir"]) < 1e-12
+            checked += 1
+    assert checked > 50
+
+
+def test_wedge_refinement_eq10_and_floor(oracle_mod):
+    """The precise algorithm on a diffraction path: after i iterations the error is below
+    R0 s^i (Eq. 10), it is the angle to the exact AOD, and with six sub-rays it reaches the
+    double-precision floor by 60 iterations."""
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4), bottom=False))
+    ab, fc = oracle_mod.wedges(S)
+    rng = np.random.default_rng(3)
+    tx, rx = np.array([-5.0, 1.5, 1.0]), np.array([1.5, -4.0, 1.2])
+    n = 32
+    tl = oracle_mod.theta_launch(n)
+    for w in range(len(fc)):
+        im = oracle_mod.wedge_image(S, tx, rx, w)
+        c0 = im["aod_dir"] + rng.normal(size=3) * 0.3 * tl
+        c0 /= np.linalg.norm(c0)
+        R0 = max(tl, _ang(c0, im["aod_dir"]))
+        for K, its in ((9, 12), (6, 60)):
+            r = oracle_mod.refine_wedge(S, tx, rx, w, c0, R0, K, its)
+            _, _, s = oracle_mod.subray_pattern(K)
+            h = r["err_hist"]
+            m = min(len(h), 40)
+            assert np.all(h[:m] <= R0 * s ** np.arange(m) * (1 + 1e-9) + 1e-15)
+            assert abs(_ang(r["dir"], im["aod_dir"]) - r["err"]) < 1e-12
+        assert r["err"] < 1e-13
+
+
+def test_rough_records_error_angle(oracle_mod):
+    """Every rough diffraction record's error angle is the angle between its ray and the
+    direction to the receiver rotated about the edge (computed here with Rodrigues'
+    formula), at most the cone; its receiver lies in the wedge's exterior."""
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4), bottom=False))
+    ab, fc = oracle_mod.wedges(S)
+    tx = np.array([-5.0, 1.5, 1.0])
+    rx = np.array([[1.5, -4.0, 1.2], [-3.0, -3.0, 6.0], [6.0, -2.0, 0.5]])
+    n = 48
+    cone = np.sqrt(3) * oracle_mod.theta_launch(n)
+    dirs = oracle_mod.lattice(n)
+    dr = oracle_mod.diffract(S, tx, dirs, rx, cone)
+    assert len(dr.rec_err) > 8
+    for i in range(len(dr.rec_err)):
+        w, r = int(dr.rec_wedge[i]), int(dr.rec_rx[i])
+        a, b = ab[w]
+        e = (b - a) / np.linalg.norm(b - a)
+        pt = (tx - a) - e * np.dot(tx - a, e)
+        pr = (rx[r] - a) - e * np.dot(rx[r] - a, e)
+        ang = np.arctan2(np.dot(np.cross(pr, -pt), e), np.dot(pr, -pt))
+        rs = _rotate(rx[r], a, e, ang)
+        d = dirs[int(dr.rec_ray[i])]
+        assert abs(_ang(d, rs - tx) - dr.rec_err[i]) < 1e-12
+        assert dr.rec_err[i] <= cone
+        assert oracle_mod.wedge_exterior(S, w, rx[r])
+
+
+@pytest.mark.parametrize("rx", [[1.5, -4.0, 1.2], [-2.0, -6.0, 2.5], [4.0, -1.0, 6.0], [6.0, 5.0, 3.0]])
+def test_pipeline_diffraction_matches_exact(oracle_mod, rx):
+    """Around one building: the rough search plus the precise algorithm and the validity
+    test return exactly the valid exact diffraction paths, each within 1e-9 rad of the
+    exact AOD and 1e-12 relative in delay after 30 iterations."""
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4), bottom=False))
+    tx = np.array([[-5.0, 1.5, 1.0]])
+    rx = np.array([rx])
+    exact = oracle_mod.wedge_enumerate(S, tx[0], rx[0])
+    res = oracle_mod.sbr_pipeline(S, tx, rx, 32, 0, np.sqrt(3), 9, 30, diffraction=True)
+    got = {p["wedge"]: p for p in res.paths if p.get("diffraction") and p["valid"]}
+    assert set(got) == set(exact)
+    for w, p in got.items():
+        assert _ang(p["ref_dir"], exact[w]["aod_dir"]) < 1e-9
+        assert abs(p["delay"] / exact[w]["delay"] - 1) < 1e-12
+        assert np.allclose(p["points"][0], exact[w]["point"], atol=1e-8)
+
+
+def test_pipeline_diffraction_in_canyon_block(oracle_mod):
+    """A 3 x 3 block of the urban canyon at a coarse lattice: every valid exact
+    diffraction path is found, and every valid refined one is a valid exact path."""
+    sc, tx, rx = scenes.urban_canyon(blocks=3)
+    S = oracle_mod.Scene.from_generated(sc)
+    rx = rx[:6]
+    res = oracle_mod.sbr_pipeline(S, tx, rx, 96, 0, np.sqrt(3), 9, 20, diffraction=True)
+    found = {(p["rx"], p["wedge"]) for p in res.paths if p.get("diffraction") and p["valid"]}
+    exact = {(r, w) for r in range(len(rx)) for w in oracle_mod.wedge_enumerate(S, tx[0], rx[r])}
+    assert len(exact) > 5
+    assert found == exact
