@@ -1318,15 +1318,16 @@ static double wedge_nearest_seen(const wedge_t *w, vec3 o, vec3 d, vec3 *x_out) 
 }
 
 /*
- * Rough order-1 diffraction search (§III.A, Fig. 4) for the rays of one Tx.  A ray's
- * first segment (from Tx to its first hit at t0, or to infinity) meets wedge w when the
- * edge point X seen at the smallest angle to the ray lies inside the ray cone (angle <=
- * cone) and not behind the first hit (foot s_X in (0, t0 (1 + tan cone)]), and Tx lies in
- * the wedge's exterior.  The diffracted rays leave X on its Keller cone; receiver r
- * receives one when it lies in the exterior, its error angle of Eq. 3 in the unfolded
- * space, angle(d, Rx* - Tx), is <= cone, and the segment X -> Rx is not blocked (the
- * wedge's two faces excluded).  Each such (ray, wedge, rx) is a record: error angle and
- * d_ray = |Rx* - Tx| cos(error).  Returns the record count (first `cap` written).
+ * Rough order-1 diffraction search (§III.A, Fig. 4) for the rays of one Tx.  A ray from
+ * Tx meets wedge w when the edge point X seen at the smallest angle to the ray lies inside
+ * the ray cone (angle <= cone) and ahead of Tx (foot s_X > 0), Tx lies in the wedge's
+ * exterior, and X is visible from Tx (the segment Tx -> X is not blocked, the wedge's two
+ * faces excluded: a ray grazing one of them just before the edge still has the edge in
+ * its cone).  The diffracted rays leave X on its Keller cone; receiver r receives one when
+ * it lies in the exterior, its error angle of Eq. 3 in the unfolded space,
+ * angle(d, Rx* - Tx), is <= cone, and the segment X -> Rx is not blocked (the wedge's faces
+ * excluded).  Each such (ray, wedge, rx) is a record: error angle and d_ray = |Rx* - Tx|
+ * cos(error).  Returns the record count (first `cap` written).
  */
 int64_t ora_diffract(void *sp, const double *tx3, const double *dirs, const int64_t *ray_ids, int64_t nrays,
                      const double *rx, int32_t nrx, double cone, int64_t cap, int32_t *rec_rx, int64_t *rec_ray,
@@ -1335,21 +1336,18 @@ int64_t ora_diffract(void *sp, const double *tx3, const double *dirs, const int6
     wedges_build(s);
     vec3 tx = ld(tx3);
     int64_t nrec = 0;
-    double tmin = 1e-7 * s->scale, tc = tan(cone);
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < nrays; ++i) {
         vec3 d = ld(dirs + 3 * i);
-        double t0;
-        int64_t hit = closest_hit(s, tx, d, -1, tmin, &t0);
-        double gate = hit >= 0 ? t0 * (1.0 + tc) : INFINITY;
         for (int wi = 0; wi < s->nw; ++wi) {
             const wedge_t *w = &s->wd[wi];
             vec3 X;
             double ang = wedge_nearest_seen(w, tx, d, &X);
             if (!(ang <= cone)) continue;
             double sx = dot(sub(X, tx), d);
-            if (!(sx > 0.0 && sx <= gate)) continue;
+            if (!(sx > 0.0)) continue;
             if (!wedge_exterior(w, tx)) continue;
+            if (occluded(s, tx, X, w->f1, w->f2)) continue;
             for (int r = 0; r < nrx; ++r) {
                 vec3 R = ld(rx + 3 * r), Rs;
                 if (!wedge_exterior(w, R) || !wedge_unfold_rx(w, tx, R, &Rs)) continue;
