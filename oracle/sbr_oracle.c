@@ -728,6 +728,16 @@ static void cone_frame(vec3 c, vec3 *u, vec3 *v) {
  * invalid the iteration stops.  Returns iterations done; writes the final direction, its
  * error, and per-iteration choice (argmin k) and error history (err_hist[0] = error of
  * c0).
+ *
+ * It also stops once the path can no longer pass the validity test's convergence
+ * condition (error <= 2 R_final + 1e-7, see ora_path_eval) -- a stalled path, whose exact
+ * direction has left the cone.  The error is the angle to the exact direction (Eq. 3 in
+ * unfolded space); every later centre lies within R (1 + s + s^2 + ...) = R / (1 - s) of
+ * the current one (sub-ray offsets are at most the cone half-angle), so later errors
+ * exceed err - R / (1 - s), while after at least one more iteration 2 R_final + 1e-7 <=
+ * 2 R s + 1e-7.  Once err > R (1 / (1 - s) + 2 s) + 1e-6 the path is rejected whatever
+ * follows, and since 1 / (1 - s) + 2 s >= 2 for every pattern it is rejected now as well.
+ * Valid paths never meet this condition, so their results are unchanged.
  */
 int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
                const double *c0, double R0, int K, int iters, double target,
@@ -740,7 +750,8 @@ int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const 
     double err = trace_planes(s, tx, rx, order, faces, c, NULL, NULL);
     if (err_hist) err_hist[0] = err;
     int it = 0;
-    while (it < iters && !(target > 0 && err <= target)) {
+    const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
+    while (it < iters && !(target > 0 && err <= target) && !(err > R * stall + 1e-6)) {
         vec3 u, v, best_d = c;
         double best = INFINITY;
         int bk = -1;
@@ -1392,7 +1403,8 @@ int ora_refine_wedge(void *sp, const double *tx3, const double *rx3, int32_t wi,
     double err = dot(c, W) > 0.0 ? angle_between(c, W) : INFINITY;
     if (err_hist) err_hist[0] = err;
     int it = 0;
-    while (it < iters && !(target > 0 && err <= target)) {
+    const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;   /* stalled paths stop, see ora_refine */
+    while (it < iters && !(target > 0 && err <= target) && !(err > R * stall + 1e-6)) {
         vec3 u, v, best_d = c;
         double best = INFINITY;
         int bk = -1;
