@@ -42,7 +42,10 @@ WORKLOADS = {
                              "5 refinement iterations, K=9",
                     gen="shoebox_config", n_div=64, max_order=3, alpha=float(np.sqrt(3.0)), iters=5, K=9, target=0.0),
 }
+WORKLOADS["canyon_diffraction"] = dict(WORKLOADS["canyon"], diffraction=True,
+                                       workload=WORKLOADS["canyon"]["workload"] + ", plus order-1 diffraction")
 WORKLOAD = WORKLOADS["canyon"]
+LAUNCH_OPTS: dict = {}   # extra sbr_launch options of the workload (diffraction)
 ACC_DEG = 0.01
 # FLOPs per unit of the trace kernel (counted from the kernel source): a 4-wide node visit
 # (four child slab tests of 6 FMA each), one watertight triangle test, one receiver
@@ -208,6 +211,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     W = WORKLOADS[args.workload]
+    LAUNCH_OPTS["diffraction"] = bool(W.get("diffraction", False))
     sc, tx, rx = getattr(scenes, W["gen"])()
     n, order, alpha, iters, K, target = (W[k] for k in ("n_div", "max_order", "alpha", "iters", "K", "target"))
     stream = torch.cuda.Stream(dev)
@@ -221,34 +225,36 @@ def run_gpu(args):
     while True:
         probe = ctx.paths_create(cap_r, cap_p)
         try:
-            ctx.launch(scene, tx_dev, rxs, probe, n, order, rx_angle_scale=alpha, sync=True)
+            ctx.launch(scene, tx_dev, rxs, probe, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS, sync=True)
             st0 = ctx.launch_stats(probe)
             break
         except api.SbrError as e:
             if e.status != 5:
                 raise
             st0 = ctx.launch_stats(probe)
-            cap_r, cap_p = max(cap_r, 2 * st0["records"]), max(cap_p, 2 * st0["paths"])
+            cap_r = max(cap_r, 2 * st0["records"], int(st0["diffraction_candidates"] / 1.25) + 1)
+            cap_p = max(cap_p, 2 * st0["paths"])
         finally:
             probe.close()
-    paths = ctx.paths_create(max(2 * st0["records"], 1024), max(2 * st0["paths"], 256))
+    paths = ctx.paths_create(max(2 * st0["records"], int(st0["diffraction_candidates"] / 1.25) + 1, 1024),
+                             max(2 * st0["paths"], 256))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     # pick the batched kernel's launch shape on these paths (autotuner)
     def relaunch():
-        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha)
+        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS)
 
     tuned = autotune.tune_batch_refine(ctx, scene, paths, relaunch, iters, K, target=target)
     shape = {k: tuned[k] for k in ("block_threads", "lanes_per_path", "blocks_per_sm")}
 
     def step():
-        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha)
+        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS)
         ctx.batch_refine(scene, paths, iters, K, target=target, **shape)
 
     # one timed (event) launch to split the step into kernels
     for _ in range(2):
         step()
-    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, timing=True)
+    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS, timing=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     ctx.batch_refine(scene, paths, iters, K, target=target, **shape)
@@ -315,9 +321,16 @@ def run_gpu(args):
            "refined_paths_per_s": good * args.steps / secs,
            "refined_paths_accurate": good, "paths": int(len(recs)),
            "valid_paths": int(np.sum(recs["valid"] == 1)),
+           "refine_iters_hist": np.bincount(recs["iters"], minlength=iters + 1).tolist(),
+           "fp64_paths": int(np.sum((recs["flags"] & 2) != 0)),
            "ray_bounces_per_step": int(st["segments"]),
            "kernel_ms": {"raygen": st_t["ms_raygen"], "trace": st_t["ms_trace"], "dedup": st_t["ms_dedup"],
-                         "batch_refine": ms_refine},
+                         "diffract": st_t["ms_diffract"], "batch_refine": ms_refine},
+           "diffraction": {"records": st_t["diffraction_records"], "wedge_tests": st_t["wedge_tests"],
+                           "candidates": st_t["diffraction_candidates"],
+                           "paths": int(np.sum((recs["order"] == 1) & (recs["faces"][:, 0] < 0))),
+                           "valid_paths": int(np.sum((recs["order"] == 1) & (recs["faces"][:, 0] < 0) &
+                                                     (recs["valid"] == 1)))} if LAUNCH_OPTS["diffraction"] else None,
            "trace_counters": {k: st_t[k] for k in ("node_visits", "tri_tests", "rx_tests", "records", "segments")},
            "refine_batched_graph_ms": batch_ms, "refine_per_pair_ms": per_pair_ms,
            "batch_refine_shape": dict(shape, tuned_ms=tuned["ms"]),
@@ -326,7 +339,8 @@ def run_gpu(args):
                         "traffic_source": None if traffic is None else traffic_rec.get("capture"),
                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} MEASURED_PEAKS.json)",
                         "flops_per_launch": flops},
-           "clocks": clocks, "gpu_launches": 6 * args.steps, "wall_s": t_wall, "e2e": e2e}
+           "clocks": clocks, "gpu_launches": (7 if LAUNCH_OPTS["diffraction"] else 6) * args.steps,
+           "wall_s": t_wall, "e2e": e2e}
     if rank == 0 and not args.no_cpu_baseline and args.workload == "canyon":
         stride = 4
         s, g, dt, nr, cores = cpu_oracle_sample(sc, tx, rx, stride)
@@ -445,11 +459,11 @@ def _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, ntx,
     """The plain per-pair form: one refinement launch per (Tx, Rx) pair from the host,
     each on the same fresh rough paths as the batched form."""
     import torch
-    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS, sync=True)
     ctx.refine_pair(scene, paths, 0, 0, iters, K, target=target)   # builds the per-pair buckets
     out = []
     for _ in range(trials if ntx * nrx <= 1024 else 1):
-        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS, sync=True)
         t = time.perf_counter()
         for tt in range(ntx):
             for r in range(nrx):
@@ -463,13 +477,13 @@ def _batched_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, strea
     """The batched form: one graph-captured persistent refinement launch for all pairs,
     timed on the host like the per-pair form, on fresh rough paths each trial."""
     import torch
-    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+    ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS, sync=True)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
         ctx.batch_refine(scene, paths, iters, K, target=target, **shape)
     out = []
     for _ in range(trials):
-        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, sync=True)
+        ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS, sync=True)
         t = time.perf_counter()
         g.replay()
         torch.cuda.synchronize()
@@ -491,7 +505,7 @@ def _e2e(ctx, scene, tx, rx, n, order, alpha, iters, K, paths, args, shape, targ
     def one():
         nonlocal nbytes_out
         rxs = ctx.rx_upload(rx_h)
-        ctx.launch(scene, tx_h, rxs, paths, n, order, rx_angle_scale=alpha)
+        ctx.launch(scene, tx_h, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS)
         ctx.batch_refine(scene, paths, iters, K, target=target, **shape)
         got = ctx.query(paths, out_h)
         nbytes_out = len(got) * 128

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define SBR_ABI_VERSION 1
+#define SBR_ABI_VERSION 2
 #define SBR_MAX_ORDER 8
 
 typedef enum {
@@ -116,6 +116,7 @@ typedef struct {
     int32_t max_leaf;
     int64_t device_bytes;
     float bbox_lo[3], bbox_hi[3];
+    int32_t num_wedges;      /* wedges found for order-1 diffraction (sbr_scene_wedges) */
 } sbr_scene_info;
 
 /* Upload a triangle scene and build its SAH BVH on the host.  verts: nv x 3 floats;
@@ -128,6 +129,16 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
                             sbr_scene **out);
 sbr_status sbr_scene_destroy(sbr_ctx *ctx, sbr_scene *scene);
 sbr_status sbr_scene_get_info(const sbr_scene *scene, sbr_scene_info *out);
+/* The scene's wedges, where rays diffract (§III.A, Fig. 4; the paper does not define a
+ * wedge, this library's reading): a side shared by two faces -- the same segment, with
+ * identical endpoint coordinates, on the boundary of both (a face's boundary triangle
+ * edges with collinear neighbours joined) -- whose half-planes meet at an interior angle
+ * between 1 and 170 degrees; the solid fills the smaller sector, rays diffract into the
+ * larger one.  Wedge ids follow the order of the face pairs (f1 < f2).  Writes
+ * min(cap, count) wedges to host arrays ab (cap x 6 floats: end a xyz, end b xyz) and
+ * faces (cap x 2: f1, f2); *count = the number of wedges.  SBR_EINVAL for null
+ * arguments or cap < 0. */
+sbr_status sbr_scene_wedges(const sbr_scene *scene, float *ab, int32_t *faces, int64_t cap, int64_t *count);
 
 /* ---------------------------------------------------------------- receivers */
 /* Upload nrx receiver positions (host, nrx x 3 floats) and build their BVH (used by the
@@ -160,6 +171,14 @@ typedef struct {
 
 #define SBR_LAUNCH_SYNC 1    /* synchronise at the end and report overflow / collisions */
 #define SBR_LAUNCH_TIMING 2  /* record CUDA events around each kernel (read by get_stats) */
+#define SBR_LAUNCH_DIFFRACTION 4 /* also search order-1 diffraction paths (§III.A, Fig. 4; §IV,
+                                    Figs. 7c-d): a ray's first segment that passes a wedge
+                                    inside its cone diffracts on the Keller cone, and a
+                                    receiver in the wedge's exterior whose Eq. 3 error angle
+                                    in the wedge's unfolded space (Rx rotated about the edge
+                                    into the half-plane opposite Tx) is within the cone and
+                                    whose segment from the edge is unblocked gets a record;
+                                    the path has order 1 and faces[0] = -1 - wedge id */
 
 typedef struct {
     int64_t rays;            /* rays traced (ntx * N) */
@@ -173,6 +192,11 @@ typedef struct {
     int32_t ntx, nrx, n_div, max_order;
     float ms_raygen, ms_trace, ms_dedup; /* device time of each kernel group (SBR_LAUNCH_TIMING), else 0 */
     int32_t trace_grid, trace_block;     /* launch shape of the trace kernel */
+    float ms_diffract;                   /* device time of the diffraction search (SBR_LAUNCH_TIMING) */
+    int64_t wedge_tests;                 /* wedges tested by the diffraction search */
+    int64_t diffraction_records;         /* diffraction records emitted */
+    int64_t diffraction_candidates;      /* (ray, wedge) candidates (may exceed candidate_cap) */
+    int64_t candidate_cap;               /* candidates the container holds: 1.25 x record_cap or more */
 } sbr_launch_stats;
 
 /* a1-a5 -- §III.A / Fig. 4: launch N rays from each of ntx transmitters (tx: ntx x 3
@@ -249,6 +273,14 @@ typedef struct {
 #define SBR_PATH_REFINED 1
 #define SBR_PATH_FP64 2      /* at least one iteration ran in FP64 */
 #define SBR_PATH_TRACE_FAIL 4 /* all sub-rays invalid at some iteration */
+#define SBR_PATH_STALLED 16   /* the refinement stopped early because the error angle exceeded
+                                 R (1 / (1 - s) + 2 s) + 1e-6: the path can no longer pass the
+                                 convergence condition and is invalid */
+#define SBR_PATH_DIFFRACTED 8 /* order-1 diffraction path: faces[0] = -1 - wedge id; the
+                                 refinement runs in the wedge's unfolded space, the validity
+                                 test asks the diffraction point to lie on the wedge, both
+                                 ends in its exterior and both legs unblocked; power is free-
+                                 space loss only (the paper gives no diffraction coefficient) */
 
 /* Number of paths in the container (synchronises). */
 sbr_status sbr_paths_count(sbr_ctx *ctx, const sbr_paths *paths, int64_t *out);

@@ -31,7 +31,8 @@ FREE_FN = _c.CFUNCTYPE(None, _vp, _c.c_size_t, _vp, _vp)
 
 class SceneInfo(_c.Structure):
     _fields_ = [("num_triangles", _i64), ("num_faces", _i32), ("bvh_nodes", _i32), ("bvh_depth", _i32),
-                ("max_leaf", _i32), ("device_bytes", _i64), ("bbox_lo", _f32 * 3), ("bbox_hi", _f32 * 3)]
+                ("max_leaf", _i32), ("device_bytes", _i64), ("bbox_lo", _f32 * 3), ("bbox_hi", _f32 * 3),
+                ("num_wedges", _i32)]
 
 
 class LaunchParams(_c.Structure):
@@ -44,7 +45,8 @@ class LaunchStats(_c.Structure):
     _fields_ = [("rays", _i64), ("segments", _i64), ("node_visits", _i64), ("tri_tests", _i64), ("rx_tests", _i64),
                 ("records", _i64), ("paths", _i64), ("collisions", _i64), ("ntx", _i32), ("nrx", _i32),
                 ("n_div", _i32), ("max_order", _i32), ("ms_raygen", _f32), ("ms_trace", _f32), ("ms_dedup", _f32),
-                ("trace_grid", _i32), ("trace_block", _i32)]
+                ("trace_grid", _i32), ("trace_block", _i32), ("ms_diffract", _f32), ("wedge_tests", _i64),
+                ("diffraction_records", _i64), ("diffraction_candidates", _i64), ("candidate_cap", _i64)]
 
 
 class RefineParams(_c.Structure):
@@ -58,7 +60,8 @@ class BatchConfig(_c.Structure):
 
 LAUNCH_SYNC = 1
 LAUNCH_TIMING = 2
-PATH_REFINED, PATH_FP64, PATH_TRACE_FAIL = 1, 2, 4
+LAUNCH_DIFFRACTION = 4
+PATH_REFINED, PATH_FP64, PATH_TRACE_FAIL, PATH_DIFFRACTED, PATH_STALLED = 1, 2, 4, 8, 16
 
 PATH_DTYPE = np.dtype([("tx", "<i4"), ("rx", "<i4"), ("ray", "<i4"), ("order", "<i4"), ("faces", "<i4", (MAX_ORDER,)),
                        ("rough_err", "<f4"), ("rough_dray", "<f4"), ("iters", "<i4"), ("valid", "<i4"),
@@ -87,6 +90,7 @@ SIGNATURES = {
     "sbr_scene_upload": (_i32, [_vp, _pf, _i64, _pi32, _pi32, _i64, _pf, _i32, _c.POINTER(_vp)]),
     "sbr_scene_destroy": (_i32, [_vp, _vp]),
     "sbr_scene_get_info": (_i32, [_vp, _c.POINTER(SceneInfo)]),
+    "sbr_scene_wedges": (_i32, [_vp, _vp, _vp, _i64, _c.POINTER(_i64)]),
     "sbr_rx_upload": (_i32, [_vp, _vp, _i32, _c.POINTER(_vp)]),
     "sbr_rx_destroy": (_i32, [_vp, _vp]),
     "sbr_paths_create": (_i32, [_vp, _i64, _i64, _c.POINTER(_vp)]),

@@ -54,6 +54,18 @@ class Scene:
         self.ctx._check(self.ctx.lib.sbr_scene_get_info(self.handle, ctypes.byref(inf)))
         return {f: (list(getattr(inf, f)) if f.startswith("bbox") else getattr(inf, f)) for f, _ in inf._fields_}
 
+    def wedges(self):
+        """The scene's wedges (order-1 diffraction): ends (W, 2, 3) float32 and face
+        pairs (W, 2) int32, in wedge-id order."""
+        cnt = ctypes.c_int64(0)
+        self.ctx._check(self.ctx.lib.sbr_scene_wedges(self.handle, None, None, 0, ctypes.byref(cnt)))
+        n = cnt.value
+        ab = np.zeros((max(n, 1), 6), np.float32)
+        fc = np.zeros((max(n, 1), 2), np.int32)
+        self.ctx._check(self.ctx.lib.sbr_scene_wedges(self.handle, ab.ctypes.data, fc.ctypes.data, n,
+                                                      ctypes.byref(cnt)))
+        return ab[:n].reshape(-1, 2, 3), fc[:n]
+
     def close(self):
         if self.handle:
             self.ctx.lib.sbr_scene_destroy(self.ctx.handle, self.handle)
@@ -186,16 +198,18 @@ class Context:
     def launch(self, scene: Scene, tx, rx: RxSet, paths: Paths, n_div: int, max_order: int,
                rx_angle_scale: float = 1.0, sync: bool = False, dump_stride: int = 0,
                dump: torch.Tensor | None = None, grid_blocks: int = 0, block_threads: int = 0,
-               timing: bool = False, refill_min: int = 0, launcher: int = 0):
+               timing: bool = False, refill_min: int = 0, launcher: int = 0, diffraction: bool = False):
         """a1-a5: ray generation, trace with reception, double-count removal.  `tx` is an
-        (ntx, 3) array on the host (numpy) or the device (torch)."""
+        (ntx, 3) array on the host (numpy) or the device (torch).  `diffraction` adds the
+        order-1 diffraction search."""
         if isinstance(tx, torch.Tensor):
             txp, ntx = tx.data_ptr(), tx.numel() // 3
             keep = tx
         else:
             keep = _host_f32(tx)
             txp, ntx = keep.ctypes.data, len(keep)
-        flags = (B.LAUNCH_SYNC if sync else 0) | (B.LAUNCH_TIMING if timing else 0)
+        flags = ((B.LAUNCH_SYNC if sync else 0) | (B.LAUNCH_TIMING if timing else 0) |
+                 (B.LAUNCH_DIFFRACTION if diffraction else 0))
         prm = B.LaunchParams(n_div, max_order, rx_angle_scale, flags, dump_stride,
                              _ptr(dump), 0 if dump is None else dump.numel(), grid_blocks, block_threads,
                              refill_min, launcher)

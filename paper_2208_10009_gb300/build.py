@@ -17,8 +17,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 SO = os.path.join(OUT, "libsbr.so")
-SOURCES = ["capi.cu", "host_geometry.cpp", "kernels_trace.cu", "kernels_paths.cu", "kernels_refine.cu",
-           "kernels_unfold.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "host_geometry.cpp", "host_wedges.cpp", "kernels_trace.cu", "kernels_diffract.cu",
+           "kernels_paths.cu", "kernels_refine.cu", "kernels_unfold.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

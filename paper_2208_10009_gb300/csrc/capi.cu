@@ -396,6 +396,28 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
         std::vector<int> cur(off.begin(), off.end() - 1);
         for (int64_t i = 0; i < nt; ++i) idx[cur[tri_face[bvh.prim_order[i]]]++] = (int)i;
     }
+    // wedges (order-1 diffraction) in id order, and a BVH over their segments
+    std::vector<WedgeHost> wl;
+    build_wedges(verts, nv, tris, tri_face, nt, nf, wl);
+    const int nw = (int)wl.size();
+    std::vector<float4> w4(4 * (size_t)std::max(nw, 1), make_float4(0, 0, 0, 0));
+    std::vector<float> wlo(3 * (size_t)nw), whi(3 * (size_t)nw);
+    for (int i = 0; i < nw; ++i) {
+        const WedgeHost &w = wl[i];
+        w4[4 * i] = make_float4(w.a[0], w.a[1], w.a[2], bits_as_float(w.f1));
+        w4[4 * i + 1] = make_float4(w.b[0], w.b[1], w.b[2], bits_as_float(w.f2));
+        w4[4 * i + 2] = make_float4((float)w.w1[0], (float)w.w1[1], (float)w.w1[2], 0.0f);
+        w4[4 * i + 3] = make_float4((float)w.w2[0], (float)w.w2[1], (float)w.w2[2], 0.0f);
+        for (int a = 0; a < 3; ++a) {
+            wlo[3 * i + a] = std::min(w.a[a], w.b[a]) - pad;
+            whi[3 * i + a] = std::max(w.a[a], w.b[a]) + pad;
+        }
+    }
+    BvhOut wbvh;
+    if (nw > 0 && !build_bvh(wlo, whi, 2, wbvh, err)) return fail(ctx, SBR_EDEGENERATE, err);
+    if (nw == 0) wbvh.nodes.assign(4, make_float4(0, 0, 0, 0));
+    std::vector<int> wids(wbvh.prim_order.begin(), wbvh.prim_order.end());
+    if (wids.empty()) wids.push_back(0);
     std::vector<float4> pl4((size_t)std::max(nf, 1));
     std::vector<float> eps((size_t)std::max(nf, 1), 0.0f);
     for (int f = 0; f < nf; ++f) {
@@ -407,7 +429,8 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     float4 *d_nodes, *d_nodes4, *d_tris, *d_pl;
     Plane64 *d_pld;
     float *d_eps;
-    int *d_off, *d_idx;
+    int *d_off, *d_idx, *d_wid;
+    float4 *d_w, *d_wn;
     Carver cv;
     cv.add(&d_nodes, bvh.nodes.size());
     cv.add(&d_nodes4, bvh.nodes4.size());
@@ -417,6 +440,9 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     cv.add(&d_eps, eps.size());
     cv.add(&d_off, off.size());
     cv.add(&d_idx, std::max<size_t>(idx.size(), 1));
+    cv.add(&d_w, w4.size());
+    cv.add(&d_wn, wbvh.nodes.size());
+    cv.add(&d_wid, wids.size());
     sc->mem = dev_alloc(ctx, cv.total);
     if (!sc->mem) {
         delete sc;
@@ -433,6 +459,9 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     SBR_CUDA(cudaMemcpyAsync(d_eps, eps.data(), eps.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     if (nt) SBR_CUDA(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    SBR_CUDA(cudaMemcpyAsync(d_w, w4.data(), w4.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+    SBR_CUDA(cudaMemcpyAsync(d_wn, wbvh.nodes.data(), wbvh.nodes.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+    SBR_CUDA(cudaMemcpyAsync(d_wid, wids.data(), wids.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaStreamSynchronize(s));
     sc->dev.nodes = d_nodes;
     sc->dev.nodes4 = d_nodes4;
@@ -446,6 +475,12 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     sc->dev.nf = nf;
     sc->dev.nnodes = (int)(bvh.nodes.size() / 4);
     sc->dev.tmin = (float)(1e-7 * diag);
+    sc->dev.wedges = d_w;
+    sc->dev.wnodes = d_wn;
+    sc->dev.wedge_bvh_ids = d_wid;
+    sc->dev.nw = nw;
+    sc->wedges = std::move(wl);
+    sc->info.num_wedges = nw;
     sc->info.num_triangles = nt;
     sc->info.num_faces = nf;
     sc->info.bvh_nodes = sc->dev.nnodes;
@@ -457,6 +492,21 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
         sc->info.bbox_hi[a] = (float)hi[a];
     }
     *out = sc;
+    return SBR_OK;
+}
+
+sbr_status sbr_scene_wedges(const sbr_scene *scene, float *ab, int32_t *faces, int64_t cap, int64_t *count) {
+    if (!scene || !count || cap < 0 || (cap > 0 && (!ab || !faces))) return SBR_EINVAL;
+    *count = (int64_t)scene->wedges.size();
+    for (int64_t i = 0; i < std::min<int64_t>(cap, *count); ++i) {
+        const WedgeHost &w = scene->wedges[i];
+        for (int a = 0; a < 3; ++a) {
+            ab[6 * i + a] = w.a[a];
+            ab[6 * i + 3 + a] = w.b[a];
+        }
+        faces[2 * i] = w.f1;
+        faces[2 * i + 1] = w.f2;
+    }
     return SBR_OK;
 }
 
@@ -658,6 +708,25 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     int grid = prm->grid_blocks > 0 ? prm->grid_blocks : ctx->num_sms * trace_blocks_per_sm(block);
     SBR_CUDA(launch_trace(a, grid, block, ctx->stream));
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
+    if (prm->flags & SBR_LAUNCH_DIFFRACTION) {
+        DiffractArgs df;
+        df.scene = scene->dev;
+        df.rx = rx->dev;
+        df.dirs = a.dirs;
+        df.tx = paths->tx;
+        df.ntx = ntx;
+        df.nrays_per_tx = N;
+        df.cone = a.cone;
+        df.tan_cone = a.tan_cone;
+        df.recs = paths->recs;
+        df.rec_cap = paths->record_cap;
+        df.counters = paths->counters;
+        // the candidate list borrows the dedup table, which is cleared after this step
+        df.cand = reinterpret_cast<float4 *>(paths->table);
+        df.cand_cap = paths->table_slots * 5 / 8;
+        SBR_CUDA(launch_diffract(df, ctx->num_sms, ctx->stream));
+    }
+    if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[4], ctx->stream));
     paths->trace_grid = grid;
     paths->trace_block = block;
     DedupArgs d;
@@ -684,7 +753,7 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
         sbr_launch_stats s;
         st = sbr_launch_get_stats(ctx, paths, &s);
         if (st != SBR_OK) return st;
-        if (s.records > paths->record_cap || s.paths > paths->path_cap)
+        if (s.records > paths->record_cap || s.paths > paths->path_cap || s.diffraction_candidates > s.candidate_cap)
             return fail(ctx, SBR_EOVERFLOW, "sbr_launch: " + std::to_string(s.records) + " records / " +
                                                 std::to_string(s.paths) + " paths exceed the container");
         if (s.collisions) return fail(ctx, SBR_ECOLLISION, "sbr_launch: dedup hash collision");
@@ -710,12 +779,17 @@ sbr_status sbr_launch_get_stats(sbr_ctx *ctx, const sbr_paths *paths, sbr_launch
     out->nrx = paths->nrx;
     out->n_div = paths->n_div;
     out->max_order = paths->max_order;
-    out->ms_raygen = out->ms_trace = out->ms_dedup = 0.0f;
+    out->ms_raygen = out->ms_trace = out->ms_dedup = out->ms_diffract = 0.0f;
     if (paths->timed && ctx->ev[0]) {
         SBR_CUDA(cudaEventElapsedTime(&out->ms_raygen, ctx->ev[0], ctx->ev[1]));
         SBR_CUDA(cudaEventElapsedTime(&out->ms_trace, ctx->ev[1], ctx->ev[2]));
-        SBR_CUDA(cudaEventElapsedTime(&out->ms_dedup, ctx->ev[2], ctx->ev[3]));
+        SBR_CUDA(cudaEventElapsedTime(&out->ms_diffract, ctx->ev[2], ctx->ev[4]));
+        SBR_CUDA(cudaEventElapsedTime(&out->ms_dedup, ctx->ev[4], ctx->ev[3]));
     }
+    out->wedge_tests = c[kWedgeTests];
+    out->diffraction_records = c[kDiffRecords];
+    out->diffraction_candidates = c[kDiffCand];
+    out->candidate_cap = paths->table_slots * 5 / 8;
     out->trace_grid = paths->trace_grid;
     out->trace_block = paths->trace_block;
     return SBR_OK;
@@ -742,6 +816,8 @@ static sbr_status refine_args(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *p
     A.max_iters = prm->max_iters;
     A.theta_launch = (float)sbr_theta_launch(paths->n_div);
     A.target = prm->target_err_rad;
+    A.tan2_target = prm->target_err_rad >= 1.5707963267948966 ? INFINITY
+                                                               : std::pow(std::tan(prm->target_err_rad), 2.0);
     A.fp64_below = prm->fp64_below_rad > 0 ? prm->fp64_below_rad : 1e-5;
     A.freq = prm->freq_hz > 0 ? prm->freq_hz : 2.4e9;
     A.ptx_dbm = prm->ptx_dbm;
@@ -750,6 +826,7 @@ static sbr_status refine_args(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *p
     A.ntx = paths->ntx;
     A.nrx = paths->nrx;
     A.nf = scene->dev.nf;
+    A.nw = scene->dev.nw;
     return SBR_OK;
 }
 

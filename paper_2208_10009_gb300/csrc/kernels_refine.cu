@@ -47,16 +47,55 @@ cudaError_t upload_subray_table(cudaStream_t s) {
 struct PathGeo {
     float3 tx, rx;
     dvec3 txd, rxd;
-    int k;
+    int k;        // planes to unfold (0 for a diffraction path)
+    int wedge;    // wedge id of a diffraction path, else -1
     int faces[kMaxOrder];
 };
 
 // Records can come from sbr_paths_import, so every id is checked before it is used.
 __device__ __forceinline__ bool path_ids_ok(const RefineArgs &A, const sbr_path_record &p) {
     if (p.tx < 0 || p.tx >= A.ntx || p.rx < 0 || p.rx >= A.nrx || p.order < 0 || p.order > kMaxOrder) return false;
+    if (p.order == 1 && p.faces[0] < 0) return -1 - p.faces[0] < A.nw;
     for (int j = 0; j < p.order; ++j)
         if (p.faces[j] < 0 || p.faces[j] >= A.nf) return false;
     return true;
+}
+
+// ------------------------------------------------------------ order-1 diffraction (wedges)
+struct WedgeD {
+    dvec3 a, b, w1, w2;
+    int f1, f2;
+};
+
+__device__ __forceinline__ WedgeD wedge64(const SceneDev &S, int id) {
+    const float4 *p = S.wedges + 4 * (size_t)id;
+    float4 A = __ldg(p), B = __ldg(p + 1), W1 = __ldg(p + 2), W2 = __ldg(p + 3);
+    return {dv(A.x, A.y, A.z), dv(B.x, B.y, B.z), dv(W1.x, W1.y, W1.z), dv(W2.x, W2.y, W2.z), __float_as_int(A.w),
+            __float_as_int(B.w)};
+}
+
+// p lies outside the interior sector (the solid) between w1 and w2; e = edge direction
+__device__ __forceinline__ bool exterior64(const WedgeD &w, dvec3 e, dvec3 p) {
+    dvec3 q = p - w.a;
+    q = q - e * ddot(q, e);
+    dvec3 n = dcross(w.w1, w.w2);
+    return !(ddot(dcross(w.w1, q), n) > 0.0 && ddot(dcross(q, w.w2), n) > 0.0);
+}
+
+// W = Rx* - Tx with Rx* = Rx rotated about the edge line into the half-plane through the
+// edge opposite Tx: the diffraction analogue of the mirror image, in whose space Eq. 3's
+// error angle of a launch direction d is angle(d, W) (zero vector if Tx is on the line)
+__device__ __forceinline__ dvec3 wedge_unfold(const SceneDev &S, int id, dvec3 tx, dvec3 rx) {
+    WedgeD w = wedge64(S, id);
+    dvec3 eb = w.b - w.a;
+    dvec3 e = eb * (1.0 / dnorm(eb));
+    dvec3 qt = tx - w.a, qr = rx - w.a;
+    dvec3 pt = qt - e * ddot(qt, e);
+    double zr = ddot(qr, e);
+    dvec3 pr = qr - e * zr;
+    double rt = dnorm(pt), rr = dnorm(pr);
+    if (!(rt > 0.0)) return dv(0.0, 0.0, 0.0);
+    return w.a + e * zr - pt * (rr / rt) - tx;
 }
 
 __device__ __forceinline__ void load_path(const RefineArgs &A, const sbr_path_record &p, PathGeo &g) {
@@ -65,59 +104,166 @@ __device__ __forceinline__ void load_path(const RefineArgs &A, const sbr_path_re
     g.rx = f3(r);
     g.txd = dv(t.x, t.y, t.z);
     g.rxd = dv(r.x, r.y, r.z);
-    g.k = p.order;
+    g.wedge = (p.order == 1 && p.faces[0] < 0) ? -1 - p.faces[0] : -1;
+    g.k = g.wedge >= 0 ? 0 : p.order;
 #pragma unroll
     for (int j = 0; j < kMaxOrder; ++j) g.faces[j] = p.faces[j];
 }
 
-// Eq. 3 error angle at Rx of direction d traced from Tx through the fixed face planes;
-// +inf if a segment length is not positive or the foot distance is not positive.
-__device__ __forceinline__ float eval32(const SceneDev &S, const PathGeo &g, float3 d) {
-    float3 o = g.tx;
-    float L = 0.0f;
-#pragma unroll
-    for (int j = 0; j < kMaxOrder; ++j) {
-        if (j >= g.k) break;
-        float4 pl = __ldg(S.planes + g.faces[j]);
-        float3 n = f3(pl);
-        float den = dot(n, d);
-        if (den == 0.0f) return INFINITY;
-        float t = (pl.w - dot(n, o)) / den;
-        if (!(t > 0.0f)) return INFINITY;
-        o = o + d * t;
-        L += t;
-        d = d - n * (2.0f * dot(d, n));
+// The sub-rays of a path are traced through its fixed face planes.  Mirroring is an
+// isometry, so that trace is a straight line in the path's unfolded space: face j's plane
+// seen through the mirrors of faces 1..j-1 is n'_j . x = h'_j, the sub-ray from Tx along d
+// meets it at T_j = num_j / (n'_j . d) with num_j = h'_j - n'_j . Tx, and the real segment
+// lengths are T_j - T_{j-1}.  The receiver's image Rx' (mirrored through faces k..1) makes
+// Eq. 3 exact in the same space: with W = Rx' - Tx the foot distance d_ray is W . d and
+// the distance of Rx from the ray d_Rx-ray is |d x W|, so the error angle is
+// atan2(|d x W|, d . W).  A sub-ray costs one dot product per face and no division; the
+// argmin compares |d x W|^2, which orders sub-rays like the angle (below pi/2; a sub-ray
+// with d . W <= 0 or a non-positive segment is invalid, as in the real-space trace).
+struct __align__(32) D4 {
+    double x, y, z, w;
+};
+struct __align__(16) UnfF {
+    float4 p[kMaxOrder];   // (n'_j, num_j)
+    float4 w;              // (W, 0)
+};
+struct __align__(32) UnfD {
+    D4 p[kMaxOrder];
+    D4 w;
+};
+
+// plane of face j seen from Tx through the mirrors of faces j-1, ..., 0 (innermost first)
+__device__ __forceinline__ D4 unfold_plane(const SceneDev &S, const PathGeo &g, int j) {
+    Plane64 pl = S.planes_d[g.faces[j]];
+    dvec3 n = dv(pl.x, pl.y, pl.z);
+    double h = pl.w;
+    for (int m = j - 1; m >= 0; --m) {
+        Plane64 q = S.planes_d[g.faces[m]];
+        dvec3 qn = dv(q.x, q.y, q.z);
+        double nm = ddot(n, qn);
+        n = n - qn * (2.0 * nm);
+        h = fma(-2.0 * nm, q.w, h);
     }
-    float3 w = g.rx - o;
-    float s = dot(w, d);
-    float3 q = w - d * s;
-    float dray = L + s;
-    if (!(dray > 0.0f)) return INFINITY;
-    return atan2f(sqrtf(dot(q, q)), dray);
+    return {n.x, n.y, n.z, h - ddot(n, g.txd)};
 }
 
-__device__ __forceinline__ double eval64(const SceneDev &S, const PathGeo &g, dvec3 d) {
-    dvec3 o = g.txd;
-    double L = 0.0;
+// W = Rx' - Tx, Rx mirrored through faces k-1, ..., 0 (rotated about the edge line for a
+// diffraction path)
+__device__ __forceinline__ D4 unfold_rx(const SceneDev &S, const PathGeo &g) {
+    if (g.wedge >= 0) {
+        dvec3 W = wedge_unfold(S, g.wedge, g.txd, g.rxd);
+        return {W.x, W.y, W.z, 0.0};
+    }
+    dvec3 x = g.rxd;
+    for (int m = g.k - 1; m >= 0; --m) {
+        Plane64 q = S.planes_d[g.faces[m]];
+        dvec3 qn = dv(q.x, q.y, q.z);
+        x = x - qn * (2.0 * (ddot(qn, x) - q.w));
+    }
+    x = x - g.txd;
+    return {x.x, x.y, x.z, 0.0};
+}
+
+__device__ __forceinline__ void set_unf(UnfD &ud, UnfF &uf, int j, const D4 &P) {
+    D4 &dst = j < kMaxOrder ? ud.p[j] : ud.w;
+    dst = P;
+    (j < kMaxOrder ? uf.p[j] : uf.w) = make_float4((float)P.x, (float)P.y, (float)P.z, (float)P.w);
+}
+
+__device__ __forceinline__ void build_unf(const SceneDev &S, const PathGeo &g, UnfD &ud, UnfF &uf) {
+    for (int j = 0; j < g.k; ++j) set_unf(ud, uf, j, unfold_plane(S, g, j));
+    set_unf(ud, uf, kMaxOrder, unfold_rx(S, g));
+}
+
+// |d x W|^2 of sub-ray d (+inf if invalid); dw = d . W
+__device__ __forceinline__ float key32(const UnfF &u, int k, float3 d, float &dw) {
+    float pn = 0.0f, pd = 1.0f;   // T_{j-1} = pn / pd, T_0 = 0
 #pragma unroll
     for (int j = 0; j < kMaxOrder; ++j) {
-        if (j >= g.k) break;
-        Plane64 pl = S.planes_d[g.faces[j]];
-        dvec3 n = dv(pl.x, pl.y, pl.z);
-        double den = ddot(n, d);
-        if (den == 0.0) return INFINITY;
-        double t = (pl.w - ddot(n, o)) / den;
-        if (!(t > 0.0)) return INFINITY;
-        o = o + d * t;
-        L += t;
-        d = d - n * (2.0 * ddot(d, n));
+        if (j >= k) break;
+        const float4 P = u.p[j];
+        const float den = fmaf(P.x, d.x, fmaf(P.y, d.y, P.z * d.z));
+        if (den == 0.0f) return INFINITY;
+        // sign(T_j - T_{j-1}) = sign(x) * sign(den * pd)
+        const float x = fmaf(P.w, pd, -pn * den);
+        const bool same = (den > 0.0f) == (pd > 0.0f);
+        if (!(same ? x > 0.0f : x < 0.0f)) return INFINITY;
+        pn = P.w;
+        pd = den;
     }
-    dvec3 w = g.rxd - o;
-    double s = ddot(w, d);
-    dvec3 q = w - d * s;
-    double dray = L + s;
-    if (!(dray > 0.0)) return INFINITY;
-    return atan2(dnorm(q), dray);
+    const float3 W = make_float3(u.w.x, u.w.y, u.w.z);
+    dw = dot(d, W);
+    if (!(dw > 0.0f)) return INFINITY;
+    const float3 c = cross(d, W);
+    return dot(c, c);
+}
+
+__device__ __forceinline__ double key64(const UnfD &u, int k, dvec3 d, double &dw) {
+    double pn = 0.0, pd = 1.0;
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j) {
+        if (j >= k) break;
+        const D4 P = u.p[j];
+        const double den = fma(P.x, d.x, fma(P.y, d.y, P.z * d.z));
+        if (den == 0.0) return INFINITY;
+        const double x = fma(P.w, pd, -pn * den);
+        const bool same = (den > 0.0) == (pd > 0.0);
+        if (!(same ? x > 0.0 : x < 0.0)) return INFINITY;
+        pn = P.w;
+        pd = den;
+    }
+    const dvec3 W = dv(u.w.x, u.w.y, u.w.z);
+    dw = ddot(d, W);
+    if (!(dw > 0.0)) return INFINITY;
+    const dvec3 c = dcross(d, W);
+    return ddot(c, c);
+}
+
+// |d x W|^2 and d . W of the cone centre in the precision of the current phase
+__device__ __forceinline__ void centre_key(const UnfD &ud, const UnfF &uf, int k, dvec3 c, bool fp64, double &key,
+                                           double &dw) {
+    if (fp64) {
+        key = key64(ud, k, c, dw);
+    } else {
+        float dwf = 0.0f;
+        key = key32(uf, k, make_float3((float)c.x, (float)c.y, (float)c.z), dwf);
+        dw = dwf;
+    }
+}
+
+// The iteration stops early once the error angle is <= target: for an angle below pi/2,
+// atan2(sqrt(key), dw) <= target  <=>  key <= dw^2 tan^2(target).
+__device__ __forceinline__ bool reached(const RefineArgs &A, double key, double dw) {
+    return A.target > 0.0 && key < INFINITY && key <= dw * dw * A.tan2_target;
+}
+
+// A stalled path stops: once its error angle exceeds R (1 / (1 - s) + 2 s) + 1e-6 it can
+// no longer meet the validity test's convergence condition (2 R_final + 1e-7), because
+// later cone centres stay within R / (1 - s) of the current one and the error is the angle
+// to the exact direction; valid paths never meet this.  (FP32 is ample against the 1e-6
+// margin.)
+__device__ __forceinline__ bool stalled(double key, double dw, double R, double stall) {
+    if (!(key < INFINITY)) return true;
+    return atan2f(sqrtf((float)key), (float)dw) > (float)(R * stall + 1e-6);
+}
+
+// Eq. 3 error angle from key and d . W, in the precision of the phase that produced them
+__device__ __forceinline__ double error_angle(double key, double dw, bool fp64) {
+    if (!(key < INFINITY)) return INFINITY;
+    return fp64 ? atan2(sqrt(key), dw) : (double)atan2f(sqrtf((float)key), (float)dw);
+}
+
+// sin and cos of a small angle (|x| <= 1e-3) from their Taylor series; the first omitted
+// terms are below 1e-27 of the result
+__device__ __forceinline__ void sincos_small(double x, double &s, double &c) {
+    const double x2 = x * x;
+    s = x * (1.0 - x2 * (1.0 / 6.0) * (1.0 - x2 * (1.0 / 20.0) * (1.0 - x2 * (1.0 / 42.0))));
+    c = 1.0 - x2 * 0.5 * (1.0 - x2 * (1.0 / 12.0) * (1.0 - x2 * (1.0 / 30.0)));
+}
+
+__device__ __forceinline__ void sincos_sub(double x, double &s, double &c) {
+    if (fabs(x) <= 1e-3) sincos_small(x, s, c);
+    else sincos(x, &s, &c);
 }
 
 // sub-cone frame: u = normalize(c x e), e the world axis with the smallest |c_i| (lowest
@@ -143,12 +289,12 @@ __device__ __forceinline__ void frame64(dvec3 c, dvec3 &u, dvec3 &v) {
 }
 
 // One iteration: returns the chosen sub-ray (or -1 if all are invalid); updates c, err.
-__device__ __forceinline__ int iterate32(const SceneDev &S, const PathGeo &g, int K, int off, double R, dvec3 &c,
-                                         double &err) {
+__device__ __forceinline__ int iterate32(const UnfF &uf, int nk, int K, int off, double R, dvec3 &c, double &key_c,
+                                         double &dw_c) {
     float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
     float3 u, v;
     frame32(cf, u, v);
-    float best = INFINITY;
+    float best = INFINITY, bdw = 0.0f;
     int bk = -1;
     float3 bd = cf;
     const float Rf = (float)R;
@@ -156,9 +302,11 @@ __device__ __forceinline__ int iterate32(const SceneDev &S, const PathGeo &g, in
         float sa, ca;
         sincosf(c_sub.rho[off + k] * Rf, &sa, &ca);
         float3 dk = cf * ca + (u * c_sub.cphi[off + k] + v * c_sub.sphi[off + k]) * sa;
-        float e = eval32(S, g, dk);
-        if (e < best) {
-            best = e;
+        float dw = 0.0f;
+        float key = key32(uf, nk, dk, dw);
+        if (key < best) {
+            best = key;
+            bdw = dw;
             bk = k;
             bd = dk;
         }
@@ -166,32 +314,36 @@ __device__ __forceinline__ int iterate32(const SceneDev &S, const PathGeo &g, in
     if (bk >= 0) {
         float inv = 1.0f / sqrtf(dot(bd, bd));
         c = dv(bd.x * inv, bd.y * inv, bd.z * inv);
-        err = best;
+        key_c = best;
+        dw_c = bdw;
     }
     return bk;
 }
 
-__device__ __forceinline__ int iterate64(const SceneDev &S, const PathGeo &g, int K, int off, double R, dvec3 &c,
-                                         double &err) {
+__device__ __forceinline__ int iterate64(const UnfD &ud, int nk, int K, int off, double R, dvec3 &c, double &key_c,
+                                         double &dw_c) {
     dvec3 u, v;
     frame64(c, u, v);
-    double best = INFINITY;
+    double best = INFINITY, bdw = 0.0;
     int bk = -1;
     dvec3 bd = c;
     for (int k = 0; k < K; ++k) {
         double sa, ca;
-        sincos(c_sub.rho_d[off + k] * R, &sa, &ca);
+        sincos_sub(c_sub.rho_d[off + k] * R, sa, ca);
         dvec3 dk = c * ca + (u * c_sub.cphi_d[off + k] + v * c_sub.sphi_d[off + k]) * sa;
-        double e = eval64(S, g, dk);
-        if (e < best) {
-            best = e;
+        double dw = 0.0;
+        double key = key64(ud, nk, dk, dw);
+        if (key < best) {
+            best = key;
+            bdw = dw;
             bk = k;
             bd = dk;
         }
     }
     if (bk >= 0) {
         c = bd * (1.0 / dnorm(bd));
-        err = best;
+        key_c = best;
+        dw_c = bdw;
     }
     return bk;
 }
@@ -244,15 +396,62 @@ __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p)
     return false;
 }
 
-__device__ __forceinline__ double fresnel_perp_abs(double ci, double eps) {
-    if (eps <= 0.0) return 1.0;
-    double r = sqrt(eps - (1.0 - ci * ci));
-    return fabs((ci - r) / (ci + r));
+// |Gamma_perp| of a Fresnel reflection at incidence cosine ci on relative permittivity eps
+__device__ __forceinline__ float fresnel_perp_abs(float ci, float eps) {
+    float r = sqrtf(eps - (1.0f - ci * ci));
+    return fabsf((ci - r) / (ci + r));
 }
 
+// (azimuth, elevation) of v; the record stores them in FP32
 __device__ __forceinline__ void az_el(dvec3 v, float *out) {
-    out[0] = (float)atan2(v.y, v.x);
-    out[1] = (float)atan2(v.z, sqrt(v.x * v.x + v.y * v.y));
+    const float x = (float)v.x, y = (float)v.y, z = (float)v.z;
+    out[0] = atan2f(y, x);
+    out[1] = atan2f(z, sqrtf(x * x + y * y));
+}
+
+// Bounce points p_j of launch direction c through the path's fixed planes (FP64), with
+// den_j = n_j . d_j (the incidence cosine up to sign) and the direction of the last leg.
+// Returns false if a segment length is not positive.
+__device__ __forceinline__ bool trace_bounces(const SceneDev &S, const PathGeo &g, dvec3 c, dvec3 *pts,
+                                              double *dens, dvec3 &d_last) {
+    dvec3 o = g.txd, d = c;
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j) {
+        if (j >= g.k) break;
+        Plane64 pl = S.planes_d[g.faces[j]];
+        dvec3 n = dv(pl.x, pl.y, pl.z);
+        double den = ddot(n, d);
+        double t = den != 0.0 ? (pl.w - ddot(n, o)) / den : -1.0;
+        if (!(t > 0.0)) return false;
+        o = o + d * t;
+        pts[j] = o;
+        dens[j] = den;
+        d = d - n * (2.0 * den);
+    }
+    d_last = d;
+    return true;
+}
+
+// a8 outputs of a traced path: delay = polyline length (FP64) / c0; AOD, AOA and power =
+// ptx + free-space loss + Fresnel reflection losses in FP32, as the record stores them
+__device__ __forceinline__ void path_outputs(const RefineArgs &A, const PathGeo &g, dvec3 c, const dvec3 *pts,
+                                             const double *dens, sbr_path_record &p) {
+    double len = 0.0;
+    for (int j = 0; j <= g.k; ++j) {
+        dvec3 from = j == 0 ? g.txd : pts[j - 1];
+        dvec3 to = j == g.k ? g.rxd : pts[j];
+        len += dnorm(to - from);
+    }
+    float gain_db = 0.0f;
+    for (int j = 0; j < g.k; ++j) {
+        float eps = __ldg(A.scene.face_eps + g.faces[j]);
+        if (eps > 0.0f) gain_db += 20.0f * log10f(fresnel_perp_abs(fabsf((float)dens[j]), eps));
+    }
+    p.delay = len / kC0;
+    az_el(c, p.aod);
+    az_el((g.k > 0 ? pts[g.k - 1] : g.txd) - g.rxd, p.aoa);
+    const float lam = (float)(kC0 / A.freq);
+    p.power_dbm = (float)A.ptx_dbm + 20.0f * log10f(lam / (4.0f * 3.14159265f * (float)len)) + gain_db;
 }
 
 // Upper bound on the final error angle of a refined path whose exact direction lies in
@@ -263,30 +462,51 @@ __device__ __forceinline__ double converged_bound(int iters, double R_final) {
     return iters > 0 ? 2.0 * R_final + 1e-7 : INFINITY;
 }
 
+// a7/a8 for a diffraction path: the diffraction point Q is the point of the edge line
+// closest to the launched ray; valid iff Q lies on the edge segment and ahead of Tx, Tx and
+// Rx lie in the wedge's exterior, the refinement converged, and Tx -> Q and Q -> Rx are
+// unblocked (the wedge's faces excluded).  delay = (|Q - Tx| + |Rx - Q|) / c0, AOD = c,
+// AOA = Q - Rx, power = ptx + free-space loss (no diffraction coefficient).
+__device__ void wedge_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, sbr_path_record &p,
+                               double err_bound) {
+    const SceneDev &S = A.scene;
+    const WedgeD w = wedge64(S, g.wedge);
+    const dvec3 eb = w.b - w.a, w0 = g.txd - w.a;
+    const double Ac = ddot(c, c), B = ddot(c, eb), C = ddot(eb, eb), D = ddot(c, w0), E = ddot(eb, w0);
+    const double den = Ac * C - B * B;
+    const double u = den != 0.0 ? (Ac * E - B * D) / den : -1.0;
+    const double sq = den != 0.0 ? (B * E - C * D) / den : -1.0;
+    const dvec3 Q = w.a + eb * u;
+    const dvec3 e = eb * (1.0 / sqrt(C));
+    bool valid = u >= 0.0 && u <= 1.0 && sq > 0.0 && exterior64(w, e, g.txd) && exterior64(w, e, g.rxd) &&
+                 p.err <= err_bound;
+    for (int j = 0; j < 2 && valid; ++j) {
+        dvec3 from = j == 0 ? g.txd : Q, seg = (j == 0 ? Q : g.rxd) - from;
+        RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
+                            make_float3((float)seg.x, (float)seg.y, (float)seg.z));
+        if (any_hit(S, r, 1e-6f, 1.0f - 1e-6f, w.f1, w.f2)) valid = false;
+    }
+    const double len = dnorm(Q - g.txd) + dnorm(g.rxd - Q);
+    p.valid = valid ? 1 : 0;
+    p.delay = len / kC0;
+    az_el(c, p.aod);
+    az_el(Q - g.rxd, p.aoa);
+    const float lam = (float)(kC0 / A.freq);
+    p.power_dbm = (float)A.ptx_dbm + 20.0f * log10f(lam / (4.0f * 3.14159265f * (float)len));
+    p.flags |= SBR_PATH_DIFFRACTED;
+}
+
 // Validity test and outputs for launch direction c; writes the result fields of p.
 __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sbr_path_record &p, double err_bound) {
     const SceneDev &S = A.scene;
-    dvec3 pts[kMaxOrder];
-    dvec3 o = g.txd, d = c;
-    bool ok = true;
-    double gain_db = 0.0;
-#pragma unroll
-    for (int j = 0; j < kMaxOrder; ++j) {
-        if (j >= g.k) break;
-        Plane64 pl = S.planes_d[g.faces[j]];
-        dvec3 n = dv(pl.x, pl.y, pl.z);
-        double den = ddot(n, d);
-        double t = den != 0.0 ? (pl.w - ddot(n, o)) / den : -1.0;
-        if (!(t > 0.0)) {
-            ok = false;
-            break;
-        }
-        o = o + d * t;
-        pts[j] = o;
-        gain_db += 20.0 * log10(fresnel_perp_abs(fabs(den), (double)__ldg(S.face_eps + g.faces[j])));
-        d = d - n * (2.0 * den);
+    if (g.wedge >= 0) {
+        wedge_finalize(A, g, c, p, err_bound);
+        return;
     }
-    if (!ok) {
+    dvec3 pts[kMaxOrder];
+    double dens[kMaxOrder];
+    dvec3 dl = c;
+    if (!trace_bounces(S, g, c, pts, dens, dl)) {
         p.valid = 0;
         p.flags |= SBR_PATH_TRACE_FAIL;
         p.delay = 0.0;
@@ -294,28 +514,20 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
     }
     // Rx must be received on the last leg (its foot lies ahead of the last bounce point)
     // and the refinement must have converged
-    bool valid = ddot(g.rxd - o, d) > 0.0 && p.err <= err_bound;
+    bool valid = ddot(g.rxd - (g.k > 0 ? pts[g.k - 1] : g.txd), dl) > 0.0 && p.err <= err_bound;
     for (int j = 0; j < g.k && valid; ++j) valid = point_in_face(S, g.faces[j], pts[j]);
-    double len = 0.0;
-    for (int j = 0; j <= g.k; ++j) {
+    for (int j = 0; j <= g.k && valid; ++j) {
         dvec3 from = j == 0 ? g.txd : pts[j - 1];
         dvec3 to = j == g.k ? g.rxd : pts[j];
         dvec3 seg = to - from;
-        len += dnorm(seg);
-        if (valid) {
-            int fa = j == 0 ? -1 : g.faces[j - 1];
-            int fb = j == g.k ? -1 : g.faces[j];
-            RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
-                                make_float3((float)seg.x, (float)seg.y, (float)seg.z));
-            if (any_hit(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) valid = false;
-        }
+        int fa = j == 0 ? -1 : g.faces[j - 1];
+        int fb = j == g.k ? -1 : g.faces[j];
+        RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
+                            make_float3((float)seg.x, (float)seg.y, (float)seg.z));
+        if (any_hit(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) valid = false;
     }
     p.valid = valid ? 1 : 0;
-    p.delay = len / kC0;
-    az_el(c, p.aod);
-    az_el((g.k > 0 ? pts[g.k - 1] : g.txd) - g.rxd, p.aoa);
-    double lam = kC0 / A.freq;
-    p.power_dbm = (float)(A.ptx_dbm + 20.0 * log10(lam / (4.0 * 3.14159265358979323846 * len)) + gain_db);
+    path_outputs(A, g, c, pts, dens, p);
 }
 
 __device__ __forceinline__ void store_result(sbr_path_record *dst, const sbr_path_record &p) {
@@ -345,6 +557,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
     const long long total = A.range ? (long long)(A.range[1] - A.range[0]) : path_count(A);
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
+    const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         long long pi = A.range ? (long long)A.index[A.range[0] + i] : i;
@@ -356,33 +569,40 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
         }
         PathGeo g;
         load_path(A, p, g);
+        UnfD ud;
+        UnfF uf;
+        build_unf(A.scene, g, ud, uf);
         dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
         double R = fmax((double)A.theta_launch, (double)p.rough_err);
-        double err = R < A.fp64_below ? eval64(A.scene, g, c)
-                                      : (double)eval32(A.scene, g, make_float3((float)c.x, (float)c.y, (float)c.z));
+        bool fp64 = R < A.fp64_below;
+        double key, dw;
+        centre_key(ud, uf, g.k, c, fp64, key, dw);
         int it = 0, flags = 0;
-        while (it < A.max_iters && !(A.target > 0.0 && err <= A.target)) {
+        while (it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
             int bk;
-            if (R < A.fp64_below) {
-                bk = iterate64(A.scene, g, A.K, off, R, c, err);
+            const bool ph = R < A.fp64_below;
+            if (ph) {
+                bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
                 flags |= SBR_PATH_FP64;
             } else {
-                bk = iterate32(A.scene, g, A.K, off, R, c, err);
+                bk = iterate32(uf, g.k, A.K, off, R, c, key, dw);
             }
             if (bk < 0) {
                 flags |= SBR_PATH_TRACE_FAIL;
                 break;
             }
+            fp64 = ph;
             if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
             R *= shrink;
             ++it;
         }
+        if (it < A.max_iters && !(flags & SBR_PATH_TRACE_FAIL) && !reached(A, key, dw)) flags |= SBR_PATH_STALLED;
         p.iters = it;
         p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
         p.dir[0] = c.x;
         p.dir[1] = c.y;
         p.dir[2] = c.z;
-        p.err = err;
+        p.err = error_angle(key, dw, fp64);
         finalize_path(A, g, c, p, converged_bound(it, R));
         store_result(A.paths + pi, p);
     }
@@ -422,8 +642,8 @@ __device__ __forceinline__ void group_argmin64(double &e, int &k, unsigned gmask
 }
 
 template <int G>
-__device__ __forceinline__ int group_iterate32(const SceneDev &S, const PathGeo &g, int K, int off, double R,
-                                               dvec3 &c, double &err, int gl, unsigned gmask) {
+__device__ __forceinline__ int group_iterate32(const UnfF &uf, int nk, int K, int off, double R, dvec3 &c,
+                                               double &key_c, double &dw_c, int gl, unsigned gmask) {
     float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
     float3 u, v;
     frame32(cf, u, v);
@@ -434,9 +654,10 @@ __device__ __forceinline__ int group_iterate32(const SceneDev &S, const PathGeo 
         float sa, ca;
         sincosf(c_sub.rho[off + k] * Rf, &sa, &ca);
         float3 dk = cf * ca + (u * c_sub.cphi[off + k] + v * c_sub.sphi[off + k]) * sa;
-        float e = eval32(S, g, dk);
-        if (e < best) {
-            best = e;
+        float dw;
+        float key = key32(uf, nk, dk, dw);
+        if (key < best) {
+            best = key;
             bk = k;
         }
     }
@@ -446,80 +667,85 @@ __device__ __forceinline__ int group_iterate32(const SceneDev &S, const PathGeo 
     float sa, ca;
     sincosf(c_sub.rho[off + bk] * Rf, &sa, &ca);
     float3 bd = cf * ca + (u * c_sub.cphi[off + bk] + v * c_sub.sphi[off + bk]) * sa;
+    float dw = 0.0f;
+    float key = key32(uf, nk, bd, dw);
     float inv = 1.0f / sqrtf(dot(bd, bd));
     c = dv(bd.x * inv, bd.y * inv, bd.z * inv);
-    err = best;
+    key_c = key;
+    dw_c = dw;
     return bk;
 }
 
 template <int G>
-__device__ __forceinline__ int group_iterate64(const SceneDev &S, const PathGeo &g, int K, int off, double R,
-                                               dvec3 &c, double &err, int gl, unsigned gmask) {
+__device__ __forceinline__ int group_iterate64(const UnfD &ud, int nk, int K, int off, double R, dvec3 &c,
+                                               double &key_c, double &dw_c, int gl, unsigned gmask) {
     dvec3 u, v;
     frame64(c, u, v);
     double best = INFINITY;
     int bk = 0x7fffffff;
     for (int k = gl; k < K; k += G) {
         double sa, ca;
-        sincos(c_sub.rho_d[off + k] * R, &sa, &ca);
+        sincos_sub(c_sub.rho_d[off + k] * R, sa, ca);
         dvec3 dk = c * ca + (u * c_sub.cphi_d[off + k] + v * c_sub.sphi_d[off + k]) * sa;
-        double e = eval64(S, g, dk);
-        if (e < best) {
-            best = e;
+        double dw;
+        double key = key64(ud, nk, dk, dw);
+        if (key < best) {
+            best = key;
             bk = k;
         }
     }
     group_argmin64<G>(best, bk, gmask);
     if (!(best < INFINITY)) return -1;
     double sa, ca;
-    sincos(c_sub.rho_d[off + bk] * R, &sa, &ca);
+    sincos_sub(c_sub.rho_d[off + bk] * R, sa, ca);
     dvec3 bd = c * ca + (u * c_sub.cphi_d[off + bk] + v * c_sub.sphi_d[off + bk]) * sa;
+    double dw = 0.0;
+    double key = key64(ud, nk, bd, dw);
     c = bd * (1.0 / dnorm(bd));
-    err = best;
+    key_c = key;
+    dw_c = dw;
     return bk;
 }
 
 // Validity and outputs with the per-bounce / per-segment queries spread over the group.
+// Lane 0 traces the bounce points once (FP64) and shares them through the group's slot
+// of shared memory (sh.p[j] = (p_j, den_j), sh.w = (direction of the last leg, ok)).
 template <int G>
 __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, sbr_path_record &p, int gl,
-                               unsigned gmask, double err_bound) {
+                               unsigned gmask, double err_bound, UnfD &sh) {
     const SceneDev &S = A.scene;
-    dvec3 pts[kMaxOrder];
-    dvec3 o = g.txd, d = c;
-    bool ok = true;
-    double gain_db = 0.0;
-#pragma unroll
-    for (int j = 0; j < kMaxOrder; ++j) {
-        if (j >= g.k) break;
-        Plane64 pl = S.planes_d[g.faces[j]];
-        dvec3 n = dv(pl.x, pl.y, pl.z);
-        double den = ddot(n, d);
-        double t = den != 0.0 ? (pl.w - ddot(n, o)) / den : -1.0;
-        if (!(t > 0.0)) {
-            ok = false;
-            break;
-        }
-        o = o + d * t;
-        pts[j] = o;
-        gain_db += 20.0 * log10(fresnel_perp_abs(fabs(den), (double)__ldg(S.face_eps + g.faces[j])));
-        d = d - n * (2.0 * den);
+    if (g.wedge >= 0) {   // group-uniform: one path per group
+        if (gl == 0) wedge_finalize(A, g, c, p, err_bound);
+        return;
     }
-    if (!ok) {
+    __syncwarp(gmask);   // every lane has finished reading the unfolded planes
+    if (gl == 0) {
+        dvec3 pts[kMaxOrder];
+        double dens[kMaxOrder];
+        dvec3 dl = c;
+        bool ok = trace_bounces(S, g, c, pts, dens, dl);
+        for (int j = 0; j < g.k; ++j) sh.p[j] = {pts[j].x, pts[j].y, pts[j].z, dens[j]};
+        sh.w = {dl.x, dl.y, dl.z, ok ? 1.0 : 0.0};
+    }
+    __syncwarp(gmask);
+    if (sh.w.w == 0.0) {
         p.valid = 0;
         p.flags |= SBR_PATH_TRACE_FAIL;
         p.delay = 0.0;
         return;
     }
+    const dvec3 last = g.k > 0 ? dv(sh.p[g.k - 1].x, sh.p[g.k - 1].y, sh.p[g.k - 1].z) : g.txd;
     // Rx must be received on the last leg (its foot lies ahead of the last bounce point)
     // and the refinement must have converged
-    bool mine_ok = ddot(g.rxd - o, d) > 0.0 && p.err <= err_bound;
-    for (int j = gl; j < g.k && mine_ok; j += G) mine_ok = point_in_face(S, g.faces[j], pts[j]);
+    bool mine_ok = ddot(g.rxd - last, dv(sh.w.x, sh.w.y, sh.w.z)) > 0.0 && p.err <= err_bound;
+    for (int j = gl; j < g.k && mine_ok; j += G)
+        mine_ok = point_in_face(S, g.faces[j], dv(sh.p[j].x, sh.p[j].y, sh.p[j].z));
     bool valid = __all_sync(gmask, mine_ok);
     mine_ok = true;
     if (valid) {
         for (int j = gl; j <= g.k && mine_ok; j += G) {
-            dvec3 from = j == 0 ? g.txd : pts[j - 1];
-            dvec3 to = j == g.k ? g.rxd : pts[j];
+            dvec3 from = j == 0 ? g.txd : dv(sh.p[j - 1].x, sh.p[j - 1].y, sh.p[j - 1].z);
+            dvec3 to = j == g.k ? g.rxd : dv(sh.p[j].x, sh.p[j].y, sh.p[j].z);
             dvec3 seg = to - from;
             int fa = j == 0 ? -1 : g.faces[j - 1];
             int fb = j == g.k ? -1 : g.faces[j];
@@ -529,25 +755,29 @@ __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
         }
         valid = __all_sync(gmask, mine_ok);
     }
-    double len = 0.0;
-    for (int j = 0; j <= g.k; ++j) {
-        dvec3 from = j == 0 ? g.txd : pts[j - 1];
-        dvec3 to = j == g.k ? g.rxd : pts[j];
-        len += dnorm(to - from);
-    }
     p.valid = valid ? 1 : 0;
-    p.delay = len / kC0;
-    az_el(c, p.aod);
-    az_el((g.k > 0 ? pts[g.k - 1] : g.txd) - g.rxd, p.aoa);
-    double lam = kC0 / A.freq;
-    p.power_dbm = (float)(A.ptx_dbm + 20.0 * log10(lam / (4.0 * 3.14159265358979323846 * len)) + gain_db);
+    if (gl == 0) {
+        dvec3 pts[kMaxOrder];
+        double dens[kMaxOrder];
+        for (int j = 0; j < g.k; ++j) {
+            pts[j] = dv(sh.p[j].x, sh.p[j].y, sh.p[j].z);
+            dens[j] = sh.p[j].w;
+        }
+        path_outputs(A, g, c, pts, dens, p);
+    }
 }
 
 template <int G>
 __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
+    // the unfolded planes of each group's current path (shared by its G lanes)
+    __shared__ UnfD s_ud[256 / G];
+    __shared__ UnfF s_uf[256 / G];
+    UnfD &ud = s_ud[threadIdx.x / G];
+    UnfF &uf = s_uf[threadIdx.x / G];
     const long long total = path_count(A);
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
+    const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
@@ -567,34 +797,44 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
         }
         PathGeo g;
         load_path(A, p, g);
+        // lanes 0..k-1 unfold one plane each and lane G-1 the receiver (k <= 8 <= G); the
+        // previous path's data is no longer read once every lane has reached this point
+        __syncwarp(gmask);
+        if (gl < g.k) set_unf(ud, uf, gl, unfold_plane(A.scene, g, gl));
+        if (gl == G - 1) set_unf(ud, uf, kMaxOrder, unfold_rx(A.scene, g));
+        __syncwarp(gmask);
         dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
         double R = fmax((double)A.theta_launch, (double)p.rough_err);
-        double err = R < A.fp64_below ? eval64(A.scene, g, c)
-                                      : (double)eval32(A.scene, g, make_float3((float)c.x, (float)c.y, (float)c.z));
+        bool fp64 = R < A.fp64_below;
+        double key, dw;
+        centre_key(ud, uf, g.k, c, fp64, key, dw);
         int it = 0, flags = 0;
-        while (it < A.max_iters && !(A.target > 0.0 && err <= A.target)) {
+        while (it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
             int bk;
-            if (R < A.fp64_below) {
-                bk = group_iterate64<G>(A.scene, g, A.K, off, R, c, err, gl, gmask);
+            const bool ph = R < A.fp64_below;
+            if (ph) {
+                bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
                 flags |= SBR_PATH_FP64;
             } else {
-                bk = group_iterate32<G>(A.scene, g, A.K, off, R, c, err, gl, gmask);
+                bk = group_iterate32<G>(uf, g.k, A.K, off, R, c, key, dw, gl, gmask);
             }
             if (bk < 0) {
                 flags |= SBR_PATH_TRACE_FAIL;
                 break;
             }
+            fp64 = ph;
             if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
             R *= shrink;
             ++it;
         }
+        if (it < A.max_iters && !(flags & SBR_PATH_TRACE_FAIL) && !reached(A, key, dw)) flags |= SBR_PATH_STALLED;
         p.iters = it;
         p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
         p.dir[0] = c.x;
         p.dir[1] = c.y;
         p.dir[2] = c.z;
-        p.err = err;
-        group_finalize<G>(A, g, c, p, gl, gmask, converged_bound(it, R));
+        p.err = error_angle(key, dw, fp64);
+        group_finalize<G>(A, g, c, p, gl, gmask, converged_bound(it, R), ud);
         if (gl == 0) store_result(A.paths + pi, p);
     }
 }

@@ -21,7 +21,7 @@ constexpr int kStack4 = 96;        // 4-wide traversal stack (the builder checks
 // Device counters of one launch (int64 each).
 enum Counter {
     kRays = 0, kSegments, kNodeVisits, kTriTests, kRxTests, kRecords, kPaths, kCollisions,
-    kRayHead, kBatchHead, kBatchDone, kErrorFlags, kNumCounters = 16
+    kRayHead, kBatchHead, kBatchDone, kErrorFlags, kWedgeTests, kDiffRecords, kDiffCand, kNumCounters = 16
 };
 
 // BVH node: both children's boxes in one 64-byte node (4 x float4).
@@ -59,6 +59,13 @@ struct SceneDev {
     const int *face_tri_idx;
     int nt, nf, nnodes;
     float tmin;               // hits need t > tmin (1e-7 x scene diagonal)
+    // wedges (order-1 diffraction): per wedge 4 float4 in wedge-id order,
+    // (a, f1 bits), (b, f2 bits), (w1, 0), (w2, 0); a BVH over them (same node layout as
+    // the scene's) whose leaves index wedge_bvh_ids
+    const float4 *wedges;
+    const float4 *wnodes;
+    const int *wedge_bvh_ids;
+    int nw;
 };
 
 struct RxDev {
@@ -86,6 +93,13 @@ struct LatticeDev {
     const float4 *layers;     // [20][nl][3]: (W_e.xyz, angle W_e -> W_{e+1})
     int n, nl;
     float edge_angle;         // theta_0
+};
+
+// Wedges of a triangle scene (host_wedges.cpp), ordered by face pair.
+struct WedgeHost {
+    float a[3], b[3];
+    double w1[3], w2[3];
+    int f1, f2;
 };
 
 // Flat-face tables for the equidistant launcher.
@@ -125,7 +139,7 @@ struct sbr_ctx {
     int poly_kind = 0;
     sbr::PolyDev poly{};
     // kernel timing events (SBR_LAUNCH_TIMING)
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 struct sbr_scene {
@@ -133,6 +147,7 @@ struct sbr_scene {
     size_t bytes = 0;
     sbr::SceneDev dev{};
     sbr_scene_info info{};
+    std::vector<sbr::WedgeHost> wedges;   // host copy (sbr_scene_wedges)
 };
 
 struct sbr_rxset {
@@ -190,6 +205,8 @@ void build_lattice_tables(int n, std::vector<float4> &ico, std::vector<int2> &ed
                           std::vector<float4> &layers, int &nl);
 // Sub-ray pattern constants.
 int subray_pattern(int K, double *rho, double *phi, double *shrink);
+bool build_wedges(const float *verts, int64_t nv, const int32_t *tris, const int32_t *tri_face, int64_t nt, int nf,
+                  std::vector<WedgeHost> &out);
 // Vertex / edge / face tables of the icosahedron (poly 20) or octahedron (poly 8).
 bool build_polyhedron(int poly, std::vector<float4> &v, std::vector<int2> &e, std::vector<int4> &f);
 
@@ -217,6 +234,22 @@ struct TraceArgs {
 };
 cudaError_t launch_trace(const TraceArgs &a, int grid, int block, cudaStream_t s);
 
+struct DiffractArgs {
+    SceneDev scene;
+    RxDev rx;
+    const float4 *dirs;
+    const float4 *tx;
+    int ntx;
+    int64_t nrays_per_tx;
+    float cone, tan_cone;
+    RecDev *recs;
+    int64_t rec_cap;
+    long long *counters;
+    float4 *cand;             // candidate (ray, wedge) list, 2 float4 each (scratch)
+    int64_t cand_cap;
+};
+cudaError_t launch_diffract(const DiffractArgs &a, int num_sms, cudaStream_t s);
+
 struct DedupArgs {
     RecDev *recs;
     int64_t rec_cap;
@@ -242,12 +275,13 @@ struct RefineArgs {
     int max_iters;
     float theta_launch;
     double target;
+    double tan2_target;       // tan^2(target) (early-stop test on |d x W|^2)
     double fp64_below;
     double freq;
     double ptx_dbm;
     int8_t *choice_log;
     int chunk;                // lanes per path in the batched kernel (8, 16, 32)
-    int ntx, nrx, nf;         // bounds of the ids a path record may hold
+    int ntx, nrx, nf, nw;     // bounds of the ids a path record may hold
 };
 cudaError_t launch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s);

@@ -1,0 +1,164 @@
+"""Order-1 diffraction on the GPU (§III.A Fig. 4, §III.B last paragraph, §IV Figs. 7c-d)
+against the oracle and the exact diffraction points: the wedge table, the rough search
+after double-count removal, the refinement in the wedge's unfolded space, the validity
+test and the outputs, through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_2208_10009_gb300 import _binding as B
+from paper_2208_10009_gb300 import scenes
+
+from parity_util import TOL_ANGLE_RAD, TOL_DELAY_REL, ang, dir_of
+
+pytestmark = pytest.mark.gpu
+SQ3 = float(np.sqrt(3.0))
+
+
+def _box(lo, hi, g=1, bottom=True):
+    b = scenes._Builder()
+    scenes.box_faces(b, lo, hi, g, bottom=bottom)
+    return b.finish()
+
+
+def _tetra():
+    v = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float)
+    b = scenes._Builder()
+    for f in ([0, 1, 2], [0, 3, 1], [0, 2, 3], [1, 3, 2]):
+        b.polygon(v[f])
+    return b.finish()
+
+
+@pytest.mark.parametrize("make", [lambda: _box((0, 0, 0), (2, 3, 4)),
+                                  lambda: _box((0, 0, 0), (2, 3, 4), g=3, bottom=False),
+                                  _tetra,
+                                  lambda: scenes.urban_canyon(blocks=3)[0],
+                                  lambda: scenes.office(nbox=40, ntx=1, nrx=3, g_shell=4, g_box=3)[0]])
+def test_wedges_match_oracle(gpu_ctx, oracle_mod, make):
+    sc = make()
+    scene = gpu_ctx.scene_from(sc)
+    ab, fc = scene.wedges()
+    oab, ofc = oracle_mod.wedges(oracle_mod.Scene.from_generated(sc))
+    assert scene.info()["num_wedges"] == len(ofc) > 0
+    assert np.array_equal(fc, ofc)
+    assert np.array_equal(ab.astype(np.float64), oab)
+    scene.close()
+
+
+def _diff_paths(recs):
+    return {(int(r["tx"]), int(r["rx"]), -1 - int(r["faces"][0])): r for r in recs
+            if r["order"] == 1 and r["faces"][0] < 0}
+
+
+@pytest.fixture(scope="module")
+def block(gpu_ctx, oracle_mod):
+    """3 x 3 blocks of the urban canyon, 6 receivers, n = 96, LOS + diffraction."""
+    sc, tx, rx = scenes.urban_canyon(blocks=3)
+    rx = rx[:6]
+    n = 96
+    S = oracle_mod.Scene.from_generated(sc)
+    scene = gpu_ctx.scene_from(sc)
+    rxs = gpu_ctx.rx_upload(rx)
+    paths = gpu_ctx.paths_create(1 << 18, 1 << 14)
+    cone = SQ3 * oracle_mod.theta_launch(n)
+    dr = oracle_mod.diffract(S, tx[0], oracle_mod.lattice(n), rx, cone)
+    ora = {(p["tx"], p["rx"], p["wedge"]): p for p in oracle_mod.dedup_wedge(dr, 0)}
+    yield sc, tx, rx, n, S, scene, rxs, paths, ora, dr
+    for h in (paths, rxs, scene):
+        h.close()
+
+
+def test_rough_diffraction_paths_match_oracle(gpu_ctx, oracle_mod, block):
+    """One path per (Tx, Rx, wedge) with the smallest error angle: the same keys, the same
+    winning ray and error angle as the oracle's brute-force search, apart from decisions
+    within rounding of a threshold (cone, first-hit gate, occlusion)."""
+    sc, tx, rx, n, S, scene, rxs, paths, ora, dr = block
+    gpu_ctx.launch(scene, tx, rxs, paths, n, 0, rx_angle_scale=SQ3, sync=True, diffraction=True)
+    st = gpu_ctx.launch_stats(paths)
+    assert st["diffraction_records"] > 0 and st["wedge_tests"] > 0 and st["collisions"] == 0
+    got = _diff_paths(gpu_ctx.query(paths))
+    assert len(ora) > 10
+    cone = SQ3 * oracle_mod.theta_launch(n)
+    only_gpu, only_ora = set(got) - set(ora), set(ora) - set(got)
+    # a key found by one side only hinges on a decision within rounding of a threshold
+    # (the cone, the first-hit gate, an occluder's edge): rare
+    assert len(only_gpu) + len(only_ora) <= max(2, len(ora) // 50), (sorted(only_gpu), sorted(only_ora))
+    same_ray = 0
+    for k in set(got) & set(ora):
+        g, o = got[k], ora[k]
+        if int(g["ray"]) == o["ray"]:
+            same_ray += 1
+            assert abs(g["rough_err"] - o["err"]) < 1e-6 * cone + 2e-7
+    assert same_ray >= 0.97 * len(set(got) & set(ora))
+
+
+def test_refined_diffraction_vs_oracle_and_exact(gpu_ctx, oracle_mod, block):
+    """After 20 iterations (K = 9): the validity flags equal the oracle's, every valid
+    path's AOD is within the parity tolerance of the exact diffraction point's, its delay
+    within 1e-6 relative, and the valid set equals the exact (image-method) valid set."""
+    sc, tx, rx, n, S, scene, rxs, paths, ora, dr = block
+    gpu_ctx.launch(scene, tx, rxs, paths, n, 0, rx_angle_scale=SQ3, sync=True, diffraction=True)
+    gpu_ctx.batch_refine(scene, paths, 20, 9)
+    got = _diff_paths(gpu_ctx.query(paths))
+    tl = oracle_mod.theta_launch(n)
+    _, _, s9 = oracle_mod.subray_pattern(9)
+    checked = 0
+    for (t, r, w), p in got.items():
+        assert p["flags"] & B.PATH_DIFFRACTED
+        R0 = max(tl, float(p["rough_err"]))
+        bound = oracle_mod.refined_err_bound(R0, 9, int(p["iters"]))
+        ev = oracle_mod.wedge_eval(S, tx[t], rx[r], w, p["dir"], err_bound=bound)
+        assert bool(p["valid"]) == ev["valid"], ((t, r, w), p["valid"], ev)
+        ex = oracle_mod.wedge_image(S, tx[t], rx[r], w)
+        if p["valid"]:
+            assert ex["valid"]
+            assert ang(p["dir"], ex["aod_dir"]) < TOL_ANGLE_RAD
+            assert abs(p["delay"] / ex["delay"] - 1) < TOL_DELAY_REL
+            assert ang(dir_of(*p["aoa"]), dir_of(*ex["aoa"])) < TOL_ANGLE_RAD
+            assert abs(p["power_dbm"] - ex["power"]) < 1e-3
+            checked += 1
+    exact = {(0, r, w) for r in range(len(rx)) for w in oracle_mod.wedge_enumerate(S, tx[0], rx[r])}
+    valid = {k for k, p in got.items() if p["valid"]}
+    assert valid == exact and checked > 5
+
+
+def test_diffraction_leaves_reflections_alone(gpu_ctx, block):
+    """The diffraction search only adds paths: the reflection paths of a launch with it
+    equal those of a launch without it."""
+    sc, tx, rx, n, S, scene, rxs, paths, ora, dr = block
+    key = lambda r: (int(r["tx"]), int(r["rx"]), int(r["order"]), tuple(int(f) for f in r["faces"][: r["order"]]))
+    gpu_ctx.launch(scene, tx, rxs, paths, n, 3, rx_angle_scale=SQ3, sync=True)
+    a = {key(r): (int(r["ray"]), float(r["rough_err"])) for r in gpu_ctx.query(paths)}
+    gpu_ctx.launch(scene, tx, rxs, paths, n, 3, rx_angle_scale=SQ3, sync=True, diffraction=True)
+    b = {key(r): (int(r["ray"]), float(r["rough_err"])) for r in gpu_ctx.query(paths)
+         if not (r["order"] == 1 and r["faces"][0] < 0)}
+    assert a == b
+
+
+def test_diffraction_full_canyon(gpu_ctx, oracle_mod):
+    """Full urban canyon (n = 700, 256 Rx, reflections up to order 6 plus diffraction):
+    every valid refined diffraction path is a valid exact path within the parity
+    tolerance, and for four receivers every valid exact diffraction path is found."""
+    sc, tx, rx = scenes.urban_canyon()
+    S = oracle_mod.Scene.from_generated(sc)
+    scene = gpu_ctx.scene_from(sc)
+    rxs = gpu_ctx.rx_upload(rx)
+    paths = gpu_ctx.paths_create(1 << 22, 1 << 19)
+    gpu_ctx.launch(scene, tx, rxs, paths, 700, 6, rx_angle_scale=SQ3, sync=True, diffraction=True)
+    gpu_ctx.batch_refine(scene, paths, 12, 9)
+    got = _diff_paths(gpu_ctx.query(paths))
+    valid = {k: p for k, p in got.items() if p["valid"]}
+    assert len(valid) > 50
+    rng = np.random.default_rng(11)
+    keys = list(valid)
+    for i in rng.choice(len(keys), size=min(60, len(keys)), replace=False):
+        t, r, w = keys[i]
+        ex = oracle_mod.wedge_image(S, tx[t], rx[r], w)
+        assert ex["valid"], keys[i]
+        assert ang(valid[keys[i]]["dir"], ex["aod_dir"]) < TOL_ANGLE_RAD
+        assert abs(valid[keys[i]]["delay"] / ex["delay"] - 1) < TOL_DELAY_REL
+    for r in (0, 37, 101, 200):
+        exact = set(oracle_mod.wedge_enumerate(S, tx[0], rx[r]))
+        found = {w for (t, rr, w) in valid if rr == r}
+        assert found == exact, (r, sorted(exact - found), sorted(found - exact))
+    for h in (paths, rxs, scene):
+        h.close()
