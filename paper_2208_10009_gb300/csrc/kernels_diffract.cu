@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) diffract_receive(DiffractArgs A) {
             c1 = A.cand[2 * c + 1];
             const WedgeF w = load_wedge(S, __float_as_int(c1.y));
             const float3 o = f3(__ldg(A.tx + __float_as_int(c1.x)));
-            vis = !any_hit(S, make_ray(o, f3(c0) - o), 1e-6f, 1.0f - 1e-6f, w.f1, w.f2);
+            vis = !any_hit4(S, make_ray(o, f3(c0) - o), 1e-6f, 1.0f - 1e-6f, w.f1, w.f2);
         }
         unsigned todo = __ballot_sync(0xffffffffu, vis);
         while (todo) {
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256) diffract_receive(DiffractArgs A) {
                 if (!(dw > 0.0f) || cc > dw * dw * t2) continue;
                 const float err = atan2f(sqrtf(cc), dw);
                 if (!(err <= A.cone)) continue;
-                if (any_hit(S, make_ray(X, R - X), 1e-6f, 1.0f - 1e-6f, w.f1, w.f2)) continue;
+                if (any_hit4(S, make_ray(X, R - X), 1e-6f, 1.0f - 1e-6f, w.f1, w.f2)) continue;
                 unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kRecords), 1ULL);
                 ++emitted;
                 if ((long long)slot >= A.rec_cap) continue;

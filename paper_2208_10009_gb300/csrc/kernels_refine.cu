@@ -219,18 +219,6 @@ __device__ __forceinline__ double key64(const UnfD &u, int k, dvec3 d, double &d
     return ddot(c, c);
 }
 
-// |d x W|^2 and d . W of the cone centre in the precision of the current phase
-__device__ __forceinline__ void centre_key(const UnfD &ud, const UnfF &uf, int k, dvec3 c, bool fp64, double &key,
-                                           double &dw) {
-    if (fp64) {
-        key = key64(ud, k, c, dw);
-    } else {
-        float dwf = 0.0f;
-        key = key32(uf, k, make_float3((float)c.x, (float)c.y, (float)c.z), dwf);
-        dw = dwf;
-    }
-}
-
 // The iteration stops early once the error angle is <= target: for an angle below pi/2,
 // atan2(sqrt(key), dw) <= target  <=>  key <= dw^2 tan^2(target).
 __device__ __forceinline__ bool reached(const RefineArgs &A, double key, double dw) {
@@ -245,6 +233,15 @@ __device__ __forceinline__ bool reached(const RefineArgs &A, double key, double 
 __device__ __forceinline__ bool stalled(double key, double dw, double R, double stall) {
     if (!(key < INFINITY)) return true;
     return atan2f(sqrtf((float)key), (float)dw) > (float)(R * stall + 1e-6);
+}
+
+__device__ __forceinline__ bool reached32(const RefineArgs &A, float key, float dw) {
+    return A.target > 0.0 && key < INFINITY && key <= dw * dw * (float)A.tan2_target;
+}
+
+__device__ __forceinline__ bool stalled32(float key, float dw, float Rf, float stall) {
+    if (!(key < INFINITY)) return true;
+    return atan2f(sqrtf(key), dw) > Rf * stall + 1e-6f;
 }
 
 // Eq. 3 error angle from key and d . W, in the precision of the phase that produced them
@@ -288,16 +285,16 @@ __device__ __forceinline__ void frame64(dvec3 c, dvec3 &u, dvec3 &v) {
     v = dcross(c, u);
 }
 
-// One iteration: returns the chosen sub-ray (or -1 if all are invalid); updates c, err.
-__device__ __forceinline__ int iterate32(const UnfF &uf, int nk, int K, int off, double R, dvec3 &c, double &key_c,
-                                         double &dw_c) {
-    float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
+// One iteration: returns the chosen sub-ray (or -1 if all are invalid); updates the cone
+// centre and its |d x W|^2 and d . W.  The FP32 phase keeps this state in FP32 registers
+// (GB300's FP64 pipe runs at 1/64 of the FP32 rate, conversions included).
+__device__ __forceinline__ int iterate32(const UnfF &uf, int nk, int K, int off, float Rf, float3 &cf, float &key_c,
+                                         float &dw_c) {
     float3 u, v;
     frame32(cf, u, v);
     float best = INFINITY, bdw = 0.0f;
     int bk = -1;
     float3 bd = cf;
-    const float Rf = (float)R;
     for (int k = 0; k < K; ++k) {
         float sa, ca;
         sincosf(c_sub.rho[off + k] * Rf, &sa, &ca);
@@ -313,7 +310,7 @@ __device__ __forceinline__ int iterate32(const UnfF &uf, int nk, int K, int off,
     }
     if (bk >= 0) {
         float inv = 1.0f / sqrtf(dot(bd, bd));
-        c = dv(bd.x * inv, bd.y * inv, bd.z * inv);
+        cf = bd * inv;
         key_c = best;
         dw_c = bdw;
     }
@@ -383,11 +380,28 @@ __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p)
                 const float4 *t = S.tris + 3 * (size_t)i;
                 float4 A = __ldg(t), B = __ldg(t + 1), C = __ldg(t + 2);
                 if (__float_as_int(A.w) != f) continue;
+                // edge functions in FP32; a sign within a generous rounding bound of zero
+                // (1e-5 x |edge| x (|p| + |p - vertex| + 1), 1-norms) is decided again in FP64
+                const float3 P = make_float3(px, py, pz), nf = make_float3((float)n.x, (float)n.y, (float)n.z);
+                const float3 ab = f3(B) - f3(A), bc = f3(C) - f3(B), ca = f3(A) - f3(C);
+                const float3 pa = P - f3(A), pb = P - f3(B), pc = P - f3(C);
+                const float ea = dot(cross(ab, pa), nf);
+                const float eb = dot(cross(bc, pb), nf);
+                const float ec = dot(cross(ca, pc), nf);
+                const float pn = fabsf(px) + fabsf(py) + fabsf(pz) + 1.0f;
+                auto bound = [&](float3 e, float3 q) {
+                    return 1e-5f * sqrtf(dot(e, e)) * (pn + fabsf(q.x) + fabsf(q.y) + fabsf(q.z));
+                };
+                const bool sure = fabsf(ea) > bound(ab, pa) && fabsf(eb) > bound(bc, pb) && fabsf(ec) > bound(ca, pc);
+                if (sure) {
+                    if ((ea > 0 && eb > 0 && ec > 0) || (ea < 0 && eb < 0 && ec < 0)) return true;
+                    continue;
+                }
                 dvec3 a = dv(A.x, A.y, A.z), b = dv(B.x, B.y, B.z), c = dv(C.x, C.y, C.z);
-                double ea = ddot(dcross(b - a, p - a), n);
-                double eb = ddot(dcross(c - b, p - b), n);
-                double ec = ddot(dcross(a - c, p - c), n);
-                if ((ea >= 0 && eb >= 0 && ec >= 0) || (ea <= 0 && eb <= 0 && ec <= 0)) return true;
+                double da = ddot(dcross(b - a, p - a), n);
+                double db = ddot(dcross(c - b, p - b), n);
+                double dc = ddot(dcross(a - c, p - c), n);
+                if ((da >= 0 && db >= 0 && dc >= 0) || (da <= 0 && db <= 0 && dc <= 0)) return true;
             }
         }
         if (sp == 0) break;
@@ -484,7 +498,7 @@ __device__ void wedge_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
         dvec3 from = j == 0 ? g.txd : Q, seg = (j == 0 ? Q : g.rxd) - from;
         RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
                             make_float3((float)seg.x, (float)seg.y, (float)seg.z));
-        if (any_hit(S, r, 1e-6f, 1.0f - 1e-6f, w.f1, w.f2)) valid = false;
+        if (any_hit4(S, r, 1e-6f, 1.0f - 1e-6f, w.f1, w.f2)) valid = false;
     }
     const double len = dnorm(Q - g.txd) + dnorm(g.rxd - Q);
     p.valid = valid ? 1 : 0;
@@ -524,7 +538,7 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
         int fb = j == g.k ? -1 : g.faces[j];
         RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
                             make_float3((float)seg.x, (float)seg.y, (float)seg.z));
-        if (any_hit(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) valid = false;
+        if (any_hit4(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) valid = false;
     }
     p.valid = valid ? 1 : 0;
     path_outputs(A, g, c, pts, dens, p);
@@ -558,6 +572,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
+    const float stallf = (float)stall;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         long long pi = A.range ? (long long)A.index[A.range[0] + i] : i;
@@ -574,29 +589,46 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
         build_unf(A.scene, g, ud, uf);
         dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
         double R = fmax((double)A.theta_launch, (double)p.rough_err);
-        bool fp64 = R < A.fp64_below;
-        double key, dw;
-        centre_key(ud, uf, g.k, c, fp64, key, dw);
+        bool fp64 = R < A.fp64_below, fail = false;
+        double key = INFINITY, dw = 0.0;
         int it = 0, flags = 0;
-        while (it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
-            int bk;
-            const bool ph = R < A.fp64_below;
-            if (ph) {
-                bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
-                flags |= SBR_PATH_FP64;
-            } else {
-                bk = iterate32(uf, g.k, A.K, off, R, c, key, dw);
+        if (!fp64) {
+            float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
+            float dwf = 0.0f, Rf = (float)R;
+            float keyf = key32(uf, g.k, cf, dwf);
+            while (it < A.max_iters && !reached32(A, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
+                   !(R < A.fp64_below)) {
+                const int bk = iterate32(uf, g.k, A.K, off, Rf, cf, keyf, dwf);
+                if (bk < 0) {
+                    fail = true;
+                    break;
+                }
+                if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+                R *= shrink;
+                Rf = (float)R;
+                ++it;
             }
+            c = dv(cf.x, cf.y, cf.z);
+            key = keyf;
+            dw = dwf;
+        } else {
+            key = key64(ud, g.k, c, dw);
+        }
+        while (!fail && R < A.fp64_below && it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
+            const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
             if (bk < 0) {
-                flags |= SBR_PATH_TRACE_FAIL;
+                fail = true;
                 break;
             }
-            fp64 = ph;
+            flags |= SBR_PATH_FP64;
+            fp64 = true;
             if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
             R *= shrink;
             ++it;
         }
-        if (it < A.max_iters && !(flags & SBR_PATH_TRACE_FAIL) && !reached(A, key, dw)) flags |= SBR_PATH_STALLED;
+        if (fail) flags |= SBR_PATH_TRACE_FAIL;
+        else if (it < A.max_iters && !(fp64 ? reached(A, key, dw) : reached32(A, (float)key, (float)dw)))
+            flags |= SBR_PATH_STALLED;
         p.iters = it;
         p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
         p.dir[0] = c.x;
@@ -642,14 +674,12 @@ __device__ __forceinline__ void group_argmin64(double &e, int &k, unsigned gmask
 }
 
 template <int G>
-__device__ __forceinline__ int group_iterate32(const UnfF &uf, int nk, int K, int off, double R, dvec3 &c,
-                                               double &key_c, double &dw_c, int gl, unsigned gmask) {
-    float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
+__device__ __forceinline__ int group_iterate32(const UnfF &uf, int nk, int K, int off, float Rf, float3 &cf,
+                                               float &key_c, float &dw_c, int gl, unsigned gmask) {
     float3 u, v;
     frame32(cf, u, v);
     float best = INFINITY;
     int bk = 0x7fffffff;
-    const float Rf = (float)R;
     for (int k = gl; k < K; k += G) {
         float sa, ca;
         sincosf(c_sub.rho[off + k] * Rf, &sa, &ca);
@@ -670,7 +700,7 @@ __device__ __forceinline__ int group_iterate32(const UnfF &uf, int nk, int K, in
     float dw = 0.0f;
     float key = key32(uf, nk, bd, dw);
     float inv = 1.0f / sqrtf(dot(bd, bd));
-    c = dv(bd.x * inv, bd.y * inv, bd.z * inv);
+    cf = bd * inv;
     key_c = key;
     dw_c = dw;
     return bk;
@@ -751,7 +781,7 @@ __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
             int fb = j == g.k ? -1 : g.faces[j];
             RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
                                 make_float3((float)seg.x, (float)seg.y, (float)seg.z));
-            if (any_hit(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) mine_ok = false;
+            if (any_hit4(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) mine_ok = false;
         }
         valid = __all_sync(gmask, mine_ok);
     }
@@ -778,6 +808,7 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
+    const float stallf = (float)stall;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
@@ -805,29 +836,46 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
         __syncwarp(gmask);
         dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
         double R = fmax((double)A.theta_launch, (double)p.rough_err);
-        bool fp64 = R < A.fp64_below;
-        double key, dw;
-        centre_key(ud, uf, g.k, c, fp64, key, dw);
+        bool fp64 = R < A.fp64_below, fail = false;
+        double key = INFINITY, dw = 0.0;
         int it = 0, flags = 0;
-        while (it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
-            int bk;
-            const bool ph = R < A.fp64_below;
-            if (ph) {
-                bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
-                flags |= SBR_PATH_FP64;
-            } else {
-                bk = group_iterate32<G>(uf, g.k, A.K, off, R, c, key, dw, gl, gmask);
+        if (!fp64) {
+            float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
+            float dwf = 0.0f, Rf = (float)R;
+            float keyf = key32(uf, g.k, cf, dwf);
+            while (it < A.max_iters && !reached32(A, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
+                   !(R < A.fp64_below)) {
+                const int bk = group_iterate32<G>(uf, g.k, A.K, off, Rf, cf, keyf, dwf, gl, gmask);
+                if (bk < 0) {
+                    fail = true;
+                    break;
+                }
+                if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+                R *= shrink;
+                Rf = (float)R;
+                ++it;
             }
+            c = dv(cf.x, cf.y, cf.z);
+            key = keyf;
+            dw = dwf;
+        } else {
+            key = key64(ud, g.k, c, dw);
+        }
+        while (!fail && R < A.fp64_below && it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
+            const int bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
             if (bk < 0) {
-                flags |= SBR_PATH_TRACE_FAIL;
+                fail = true;
                 break;
             }
-            fp64 = ph;
+            flags |= SBR_PATH_FP64;
+            fp64 = true;
             if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
             R *= shrink;
             ++it;
         }
-        if (it < A.max_iters && !(flags & SBR_PATH_TRACE_FAIL) && !reached(A, key, dw)) flags |= SBR_PATH_STALLED;
+        if (fail) flags |= SBR_PATH_TRACE_FAIL;
+        else if (it < A.max_iters && !(fp64 ? reached(A, key, dw) : reached32(A, (float)key, (float)dw)))
+            flags |= SBR_PATH_STALLED;
         p.iters = it;
         p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
         p.dir[0] = c.x;

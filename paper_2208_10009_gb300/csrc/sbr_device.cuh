@@ -326,6 +326,62 @@ __device__ __forceinline__ bool any_hit(const SceneDev &S, const RayPre &r, floa
     return false;
 }
 
+// Any hit of the segment o + t d, t in (tmin, tmax), ignoring faces fa and fb, over the
+// 4-wide BVH (the same triangles and the same triangle test as any_hit, so the same
+// answer, with fewer node visits).
+__device__ __forceinline__ bool any_hit4(const SceneDev &S, const RayPre &r, float tmin, float tmax, int fa, int fb) {
+    int stack[kStack4];
+    int sp = 0;
+    int node = 0;
+    const float oix = r.o.x * r.inv.x, oiy = r.o.y * r.inv.y, oiz = r.o.z * r.inv.z;
+    for (;;) {
+        if (!is_leaf(node)) {
+            const float4 *nd = S.nodes4 + 8 * (size_t)node;
+            float4 nxv = __ldg(nd + r.nx), fxv = __ldg(nd + 1 - r.nx);
+            float4 nyv = __ldg(nd + 2 + r.ny), fyv = __ldg(nd + 3 - r.ny);
+            float4 nzv = __ldg(nd + 4 + r.nz), fzv = __ldg(nd + 5 - r.nz);
+            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 6));
+            const float2 nx01 = fma2s(nxv.x, nxv.y, r.inv.x, -oix), nx23 = fma2s(nxv.z, nxv.w, r.inv.x, -oix);
+            const float2 fx01 = fma2s(fxv.x, fxv.y, r.inv.x, -oix), fx23 = fma2s(fxv.z, fxv.w, r.inv.x, -oix);
+            const float2 ny01 = fma2s(nyv.x, nyv.y, r.inv.y, -oiy), ny23 = fma2s(nyv.z, nyv.w, r.inv.y, -oiy);
+            const float2 fy01 = fma2s(fyv.x, fyv.y, r.inv.y, -oiy), fy23 = fma2s(fyv.z, fyv.w, r.inv.y, -oiy);
+            const float2 nz01 = fma2s(nzv.x, nzv.y, r.inv.z, -oiz), nz23 = fma2s(nzv.z, nzv.w, r.inv.z, -oiz);
+            const float2 fz01 = fma2s(fzv.x, fzv.y, r.inv.z, -oiz), fz23 = fma2s(fzv.z, fzv.w, r.inv.z, -oiz);
+            const float tnx[4] = {nx01.x, nx01.y, nx23.x, nx23.y}, tfx[4] = {fx01.x, fx01.y, fx23.x, fx23.y};
+            const float tny[4] = {ny01.x, ny01.y, ny23.x, ny23.y}, tfy[4] = {fy01.x, fy01.y, fy23.x, fy23.y};
+            const float tnz[4] = {nz01.x, nz01.y, nz23.x, nz23.y}, tfz[4] = {fz01.x, fz01.y, fz23.x, fz23.y};
+            const int rf[4] = {refs.x, refs.y, refs.z, refs.w};
+            int next = 0x7fffffff;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float tn = max3f(tnx[c], tny[c], fmaxf(tnz[c], tmin));
+                float tf = min3f(tfx[c], tfy[c], fminf(tfz[c], tmax)) * 1.0000005f;
+                if (tn <= tf) {
+                    if (next == 0x7fffffff) next = rf[c];
+                    else stack[sp++] = rf[c];
+                }
+            }
+            if (next != 0x7fffffff) {
+                node = next;
+                continue;
+            }
+        } else {
+            int first = leaf_first(node), cnt = leaf_count(node);
+            for (int i = first; i < first + cnt; ++i) {
+                const float4 *t = S.tris + 3 * (size_t)i;
+                float4 a = __ldg(t), b = __ldg(t + 1), c = __ldg(t + 2);
+                int f = __float_as_int(a.w);
+                if (f == fa || f == fb) continue;
+                float th = tri_watertight(r, a, b, c);
+                if (th > tmin && th < tmax) return true;
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    return false;
+}
+
 // Largest foot parameter s = (p - o).d of any point p of box [lo, hi].
 __device__ __forceinline__ float max_foot(const RxDev &R, float3 o, float3 d) {
     float s = (d.x > 0 ? R.hi[0] : R.lo[0]) * d.x + (d.y > 0 ? R.hi[1] : R.lo[1]) * d.y +
