@@ -823,6 +823,7 @@ static sbr_status refine_args(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *p
     A.ptx_dbm = prm->ptx_dbm;
     A.choice_log = prm->choice_log;
     A.chunk = 1;
+    A.split_min = 16LL * 32 * std::max(ctx->num_sms, 1);   // 16 warps of paths per SM
     A.ntx = paths->ntx;
     A.nrx = paths->nrx;
     A.nf = scene->dev.nf;

@@ -642,11 +642,11 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
 
 // a9: persistent work-queue form.  A group of G lanes (G = 8, 16 or 32) owns one path at a
 // time: lane l evaluates the sub-rays k = l, l + G, ... of each iteration and the group
-// takes the argmin with shuffles (lowest k on ties, as in the plain form); the validity
-// queries of the path (one point-in-face per bounce, one occlusion test per segment) are
-// spread over the lanes the same way.  When a path is finished (iteration cap, target
-// reached, or all sub-rays invalid) the group takes the next path index from the device
-// queue head with one atomic, so paths that stop early free their group at once.
+// takes the argmin with shuffles (lowest k on ties, as in the plain form).  When a path is
+// finished (iteration cap, target reached, stalled, or all sub-rays invalid) the group
+// takes the next path index from the device queue head with one atomic, so paths that stop
+// early free their group at once.  The validity test and outputs follow in
+// batch_finalize_kernel.
 template <int G>
 __device__ __forceinline__ void group_argmin(float &e, int &k, unsigned gmask) {
 #pragma unroll
@@ -882,8 +882,48 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
         p.dir[1] = c.y;
         p.dir[2] = c.z;
         p.err = error_angle(key, dw, fp64);
-        group_finalize<G>(A, g, c, p, gl, gmask, converged_bound(it, R), ud);
-        if (gl == 0) store_result(A.paths + pi, p);
+        if (gl == 0) {
+            // iteration results; the validity test and outputs follow in batch_finalize_kernel
+            sbr_path_record *dst = A.paths + pi;
+            dst->iters = p.iters;
+            dst->dir[0] = p.dir[0];
+            dst->dir[1] = p.dir[1];
+            dst->dir[2] = p.dir[2];
+            dst->err = p.err;
+            dst->flags = p.flags;
+        }
+    }
+}
+
+// a7/a8 of the batched form.  With many paths (>= split_min), one thread per path: every
+// lane of a warp runs the same validity test and FP64 bounce-point trace on its own path,
+// so GB300's narrow FP64 pipe serves 32 paths per instruction.  With few paths, one warp
+// per path with the point-in-face and occlusion queries spread over its lanes (latency).
+// The cone radius after `iters` iterations is recomputed with the same multiplications.
+__global__ void __launch_bounds__(128) batch_finalize_kernel(RefineArgs A) {
+    __shared__ UnfD s_sh[4];
+    const long long total = path_count(A);
+    const double shrink = c_sub.shrink[A.K];
+    const bool per_thread = total >= A.split_min;
+    const long long stride = per_thread ? (long long)gridDim.x * blockDim.x : (long long)gridDim.x * (blockDim.x >> 5);
+    const long long first = per_thread ? blockIdx.x * (long long)blockDim.x + threadIdx.x
+                                       : blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (long long pi = first; pi < total; pi += stride) {
+        sbr_path_record p = A.paths[pi];
+        if (!path_ids_ok(A, p)) continue;   // already flagged by the iteration kernel
+        PathGeo g;
+        load_path(A, p, g);
+        double R = fmax((double)A.theta_launch, (double)p.rough_err);
+        for (int i = 0; i < p.iters; ++i) R *= shrink;
+        dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
+        if (per_thread) {
+            finalize_path(A, g, c, p, converged_bound(p.iters, R));
+            store_result(A.paths + pi, p);
+        } else {
+            const int lane = threadIdx.x & 31;
+            group_finalize<32>(A, g, c, p, lane, 0xffffffffu, converged_bound(p.iters, R), s_sh[threadIdx.x >> 5]);
+            if (lane == 0) store_result(A.paths + pi, p);
+        }
     }
 }
 
@@ -920,6 +960,17 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
         case 32: batch_refine_kernel<32><<<grid, block, 0, s>>>(a); break;
         default: batch_refine_kernel<16><<<grid, block, 0, s>>>(a); break;
     }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    static int fin_blocks = 0;
+    if (!fin_blocks) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fin_blocks, batch_finalize_kernel, 128, 0);
+        if (fin_blocks < 1) fin_blocks = 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    batch_finalize_kernel<<<sms * fin_blocks, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -14,7 +14,8 @@ namespace sbr {
 
 constexpr int kMaxOrder = SBR_MAX_ORDER;
 constexpr double kC0 = 299792458.0;
-constexpr int kLeafMax = 4;        // triangles per BVH leaf (target)
+constexpr int kLeafMax = 2;        // triangles per BVH leaf (target; 2 measured fastest: a
+                                   // triangle test costs about half a 4-wide node visit)
 constexpr int kStackDepth = 64;    // traversal stack entries (BVH depth is capped below this)
 constexpr int kStack4 = 96;        // 4-wide traversal stack (the builder checks the bound)
 
@@ -281,6 +282,8 @@ struct RefineArgs {
     double ptx_dbm;
     int8_t *choice_log;
     int chunk;                // lanes per path in the batched kernel (8, 16, 32)
+    long long split_min;      // batched form: from this many paths on, validity and outputs run
+                              // one thread per path in a second kernel
     int ntx, nrx, nf, nw;     // bounds of the ids a path record may hold
 };
 cudaError_t launch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s);
