@@ -614,6 +614,7 @@ sbr_status sbr_paths_create(sbr_ctx *ctx, int64_t record_cap, int64_t path_cap, 
     Carver cv;
     cv.add(&p->recs, (size_t)record_cap);
     cv.add(&p->paths, (size_t)path_cap);
+    cv.add(&p->unf, (size_t)path_cap * 9);
     cv.add(&table, (size_t)slots * 2 + (size_t)(slots + 1) / 2);   // keys, values, winner ids
     cv.add(&p->counters, (size_t)kNumCounters);
     p->mem = dev_alloc(ctx, cv.total);
@@ -808,6 +809,7 @@ static sbr_status refine_args(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *p
     A.tx = paths->tx;
     A.rx = paths->rx->dev.by_id;
     A.paths = paths->paths;
+    A.unf = paths->unf;
     A.counters = paths->counters;
     A.path_cap = paths->path_cap;
     A.range = nullptr;

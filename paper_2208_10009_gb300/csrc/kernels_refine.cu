@@ -805,6 +805,7 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
     UnfD &ud = s_ud[threadIdx.x / G];
     UnfF &uf = s_uf[threadIdx.x / G];
     const long long total = path_count(A);
+    const bool prebuilt = total >= A.split_min;   // batch_unfold_kernel ran
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
@@ -828,11 +829,18 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
         }
         PathGeo g;
         load_path(A, p, g);
-        // lanes 0..k-1 unfold one plane each and lane G-1 the receiver (k <= 8 <= G); the
-        // previous path's data is no longer read once every lane has reached this point
+        // the path's unfolded planes and W into the group's shared slot: with many paths
+        // the FP32 copy computed by batch_unfold_kernel, with few computed here in FP64 by
+        // lanes 0..k-1 (one plane each) and lane G-1 (the receiver; k <= 8 <= G).  The
+        // previous path's data is no longer read once every lane has reached this point.
         __syncwarp(gmask);
-        if (gl < g.k) set_unf(ud, uf, gl, unfold_plane(A.scene, g, gl));
-        if (gl == G - 1) set_unf(ud, uf, kMaxOrder, unfold_rx(A.scene, g));
+        if (prebuilt) {
+            for (int j = gl; j <= kMaxOrder; j += G)
+                if (j < g.k || j == kMaxOrder) (j < kMaxOrder ? uf.p[j] : uf.w) = A.unf[9 * pi + j];
+        } else {
+            if (gl < g.k) set_unf(ud, uf, gl, unfold_plane(A.scene, g, gl));
+            if (gl == G - 1) set_unf(ud, uf, kMaxOrder, unfold_rx(A.scene, g));
+        }
         __syncwarp(gmask);
         dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
         double R = fmax((double)A.theta_launch, (double)p.rough_err);
@@ -858,8 +866,15 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
             c = dv(cf.x, cf.y, cf.z);
             key = keyf;
             dw = dwf;
-        } else {
-            key = key64(ud, g.k, c, dw);
+        }
+        if (!fail && R < A.fp64_below) {
+            // the FP64 phase needs the FP64 planes: built here if only the FP32 copy was read
+            if (prebuilt) {
+                if (gl < g.k) ud.p[gl] = unfold_plane(A.scene, g, gl);
+                if (gl == G - 1) ud.w = unfold_rx(A.scene, g);
+                __syncwarp(gmask);
+            }
+            if (fp64) key = key64(ud, g.k, c, dw);
         }
         while (!fail && R < A.fp64_below && it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
             const int bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
@@ -892,6 +907,30 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
             dst->err = p.err;
             dst->flags = p.flags;
         }
+    }
+}
+
+// Batched form, first pass (from split_min paths on), one thread per path: the FP64
+// unfolding of the path's face planes into Tx's space and of the receiver (the same
+// arithmetic as the plain form's build_unf), stored rounded to FP32 for the iteration
+// kernel.  GB300 runs FP64 at 1/64 of
+// the FP32 rate; with one path per lane every FP64 instruction serves 32 paths, where the
+// iteration kernel's lane groups would serve one.
+__global__ void __launch_bounds__(128) batch_unfold_kernel(RefineArgs A) {
+    const long long total = path_count(A);
+    if (total < A.split_min) return;   // few paths: the iteration kernel unfolds them itself
+    for (long long pi = blockIdx.x * (long long)blockDim.x + threadIdx.x; pi < total;
+         pi += (long long)gridDim.x * blockDim.x) {
+        const sbr_path_record p = A.paths[pi];
+        if (!path_ids_ok(A, p)) continue;
+        PathGeo g;
+        load_path(A, p, g);
+        for (int j = 0; j < g.k; ++j) {
+            const D4 P = unfold_plane(A.scene, g, j);
+            A.unf[9 * pi + j] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)P.w);
+        }
+        const D4 W = unfold_rx(A.scene, g);
+        A.unf[9 * pi + kMaxOrder] = make_float4((float)W.x, (float)W.y, (float)W.z, (float)W.w);
     }
 }
 
@@ -955,6 +994,15 @@ cudaError_t launch_refine(const RefineArgs &a, int grid, int block, cudaStream_t
 cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.counters + kBatchHead, 0, sizeof(long long), s);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static int unf_blocks = 0;
+    if (!unf_blocks) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&unf_blocks, batch_unfold_kernel, 128, 0);
+        if (unf_blocks < 1) unf_blocks = 1;
+    }
+    batch_unfold_kernel<<<sms * unf_blocks, 128, 0, s>>>(a);
     switch (a.chunk) {
         case 8: batch_refine_kernel<8><<<grid, block, 0, s>>>(a); break;
         case 32: batch_refine_kernel<32><<<grid, block, 0, s>>>(a); break;
@@ -967,9 +1015,6 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fin_blocks, batch_finalize_kernel, 128, 0);
         if (fin_blocks < 1) fin_blocks = 1;
     }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     batch_finalize_kernel<<<sms * fin_blocks, 128, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -164,6 +164,7 @@ struct sbr_paths {
     size_t bytes = 0;
     sbr::RecDev *recs = nullptr;
     sbr_path_record *paths = nullptr;
+    float4 *unf = nullptr;                 // batched refinement: each path's unfolded planes (9 float4)
     unsigned long long *table = nullptr;   // dedup hash table: 2 x u64 per slot (key, value)
     int64_t table_slots = 0;
     long long *counters = nullptr;         // sbr::kNumCounters
@@ -281,6 +282,7 @@ struct RefineArgs {
     double freq;
     double ptx_dbm;
     int8_t *choice_log;
+    float4 *unf;              // per path: FP32 unfolded planes and W (9 float4), batched form
     int chunk;                // lanes per path in the batched kernel (8, 16, 32)
     long long split_min;      // batched form: from this many paths on, validity and outputs run
                               // one thread per path in a second kernel
