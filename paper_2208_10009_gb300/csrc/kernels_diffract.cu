@@ -13,8 +13,8 @@
 // -1 - wedge id) to the launch's record buffer, before double-count removal.
 //
 // Candidate wedges come from a BVH over the wedge segments, each node box grown by
-// tan(cone) times the distance from Tx to its farthest corner: every point of the box
-// inside the ray cone then lies within that margin of the ray.
+// tan(cone) times the largest foot of its corners on the ray: every point of the box
+// inside the ray cone then lies within that margin of the ray (see cone_box).
 #include "sbr_device.cuh"
 
 namespace sbr {
@@ -69,19 +69,21 @@ __device__ __forceinline__ float nearest_seen(const WedgeF &w, float3 o, float3 
     return best;
 }
 
-// child box of a 2-wide node grown by tan_cone x (distance from o to its farthest corner),
-// slab-tested against the ray t >= 0
+// Child box of a 2-wide node against the ray cone.  A box point X inside the cone has its
+// foot s_X on the ray between 0 and s_max, the largest foot of any box corner, and lies
+// within s_X tan(cone) <= s_max tan(cone) of the ray; so the box grown by that radius
+// (plus a relative rounding margin) must meet the ray segment t in [0, s_max].  od = o . d.
 __device__ __forceinline__ bool cone_box(float lx, float ly, float lz, float hx, float hy, float hz, const RayPre &r,
-                                         float tan_cone) {
-    const float dx = fmaxf(fabsf(lx - r.o.x), fabsf(hx - r.o.x));
-    const float dy = fmaxf(fabsf(ly - r.o.y), fabsf(hy - r.o.y));
-    const float dz = fmaxf(fabsf(lz - r.o.z), fabsf(hz - r.o.z));
-    const float g = sqrtf(dx * dx + dy * dy + dz * dz) * tan_cone;
+                                         float od, float tan_cone) {
+    const float smax = (r.d.x > 0.0f ? hx : lx) * r.d.x + (r.d.y > 0.0f ? hy : ly) * r.d.y +
+                       (r.d.z > 0.0f ? hz : lz) * r.d.z - od;
+    if (!(smax > 0.0f)) return false;
+    const float g = smax * (tan_cone * 1.001f + 1e-6f);
     const float t0x = (lx - g - r.o.x) * r.inv.x, t1x = (hx + g - r.o.x) * r.inv.x;
     const float t0y = (ly - g - r.o.y) * r.inv.y, t1y = (hy + g - r.o.y) * r.inv.y;
     const float t0z = (lz - g - r.o.z) * r.inv.z, t1z = (hz + g - r.o.z) * r.inv.z;
     const float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.0f));
-    const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fmaxf(t0z, t1z));
+    const float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), smax * 1.000001f + g));
     return tn <= tf;
 }
 
@@ -104,6 +106,7 @@ __global__ void __launch_bounds__(128) diffract_candidates(DiffractArgs A) {
         const float3 o = f3(__ldg(A.tx + txi));
         const float3 d = f3(__ldg(A.dirs + ray));
         const RayPre r = make_ray(o, d);
+        const float od = dot(o, d);
         int stack[kStackDepth];
         int sp = 0, node = 0, li = 0, ln = 0;
         for (;;) {
@@ -132,8 +135,8 @@ __global__ void __launch_bounds__(128) diffract_candidates(DiffractArgs A) {
                     const float4 *nd = S.wnodes + 4 * (size_t)node;
                     float4 p = __ldg(nd), q = __ldg(nd + 1), t = __ldg(nd + 2);
                     int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 3));
-                    bool in0 = cone_box(p.x, p.y, p.z, p.w, q.x, q.y, r, A.tan_cone);
-                    bool in1 = cone_box(q.z, q.w, t.x, t.y, t.z, t.w, r, A.tan_cone);
+                    bool in0 = cone_box(p.x, p.y, p.z, p.w, q.x, q.y, r, od, A.tan_cone);
+                    bool in1 = cone_box(q.z, q.w, t.x, t.y, t.z, t.w, r, od, A.tan_cone);
                     if (in0 && in1) {
                         stack[sp++] = refs.y;
                         node = refs.x;
