@@ -615,6 +615,8 @@ sbr_status sbr_paths_create(sbr_ctx *ctx, int64_t record_cap, int64_t path_cap, 
     cv.add(&p->recs, (size_t)record_cap);
     cv.add(&p->paths, (size_t)path_cap);
     cv.add(&p->unf, (size_t)path_cap * 9);
+    cv.add(&p->order_idx, (size_t)path_cap);
+    cv.add(&p->order_cnt, (size_t)32);
     cv.add(&table, (size_t)slots * 2 + (size_t)(slots + 1) / 2);   // keys, values, winner ids
     cv.add(&p->counters, (size_t)kNumCounters);
     p->mem = dev_alloc(ctx, cv.total);
@@ -810,6 +812,8 @@ static sbr_status refine_args(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *p
     A.rx = paths->rx->dev.by_id;
     A.paths = paths->paths;
     A.unf = paths->unf;
+    A.order_idx = paths->order_idx;
+    A.order_cnt = paths->order_cnt;
     A.counters = paths->counters;
     A.path_cap = paths->path_cap;
     A.range = nullptr;

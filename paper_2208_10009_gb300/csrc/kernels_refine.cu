@@ -52,6 +52,9 @@ struct PathGeo {
     int faces[kMaxOrder];
 };
 
+// group of a path for the batched form's finalize lists: its order 0..8, diffraction 9
+__device__ __forceinline__ int order_group(const PathGeo &g) { return g.wedge >= 0 ? 9 : g.k; }
+
 // Records can come from sbr_paths_import, so every id is checked before it is used.
 __device__ __forceinline__ bool path_ids_ok(const RefineArgs &A, const sbr_path_record &p) {
     if (p.tx < 0 || p.tx >= A.ntx || p.rx < 0 || p.rx >= A.nrx || p.order < 0 || p.order > kMaxOrder) return false;
@@ -898,6 +901,15 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
         p.dir[2] = c.z;
         p.err = error_angle(key, dw, fp64);
         if (gl == 0) {
+            if (prebuilt) {
+                // list the path in its order group (group offsets from batch_unfold_kernel's
+                // counts), so that the finalize kernel's warps see paths of one order
+                const int grp = order_group(g);
+                unsigned long long at = 0;
+                for (int b = 0; b < grp; ++b) at += A.order_cnt[b];
+                at += atomicAdd(A.order_cnt + 16 + grp, 1ULL);
+                A.order_idx[at] = (int)pi;
+            }
             // iteration results; the validity test and outputs follow in batch_finalize_kernel
             sbr_path_record *dst = A.paths + pi;
             dst->iters = p.iters;
@@ -916,15 +928,21 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
 // kernel.  GB300 runs FP64 at 1/64 of
 // the FP32 rate; with one path per lane every FP64 instruction serves 32 paths, where the
 // iteration kernel's lane groups would serve one.
+// It also counts the paths of each order group so that the iteration kernel can list them
+// group by group for the finalize kernel.
 __global__ void __launch_bounds__(128) batch_unfold_kernel(RefineArgs A) {
+    __shared__ unsigned hist[10];
     const long long total = path_count(A);
     if (total < A.split_min) return;   // few paths: the iteration kernel unfolds them itself
+    if (threadIdx.x < 10) hist[threadIdx.x] = 0;
+    __syncthreads();
     for (long long pi = blockIdx.x * (long long)blockDim.x + threadIdx.x; pi < total;
          pi += (long long)gridDim.x * blockDim.x) {
         const sbr_path_record p = A.paths[pi];
         if (!path_ids_ok(A, p)) continue;
         PathGeo g;
         load_path(A, p, g);
+        atomicAdd(&hist[order_group(g)], 1u);
         for (int j = 0; j < g.k; ++j) {
             const D4 P = unfold_plane(A.scene, g, j);
             A.unf[9 * pi + j] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)P.w);
@@ -932,6 +950,8 @@ __global__ void __launch_bounds__(128) batch_unfold_kernel(RefineArgs A) {
         const D4 W = unfold_rx(A.scene, g);
         A.unf[9 * pi + kMaxOrder] = make_float4((float)W.x, (float)W.y, (float)W.z, (float)W.w);
     }
+    __syncthreads();
+    if (threadIdx.x < 10 && hist[threadIdx.x]) atomicAdd(A.order_cnt + threadIdx.x, (unsigned long long)hist[threadIdx.x]);
 }
 
 // a7/a8 of the batched form.  With many paths (>= split_min), one thread per path: every
@@ -947,7 +967,13 @@ __global__ void __launch_bounds__(128) batch_finalize_kernel(RefineArgs A) {
     const long long stride = per_thread ? (long long)gridDim.x * blockDim.x : (long long)gridDim.x * (blockDim.x >> 5);
     const long long first = per_thread ? blockIdx.x * (long long)blockDim.x + threadIdx.x
                                        : blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (long long pi = first; pi < total; pi += stride) {
+    long long listed = total;
+    if (per_thread) {   // paths with valid ids, listed by order group by the iteration kernel
+        listed = 0;
+        for (int b = 0; b < 10; ++b) listed += A.order_cnt[b];
+    }
+    for (long long t = first; t < listed; t += stride) {
+        const long long pi = per_thread ? (long long)A.order_idx[t] : t;
         sbr_path_record p = A.paths[pi];
         if (!path_ids_ok(A, p)) continue;   // already flagged by the iteration kernel
         PathGeo g;
@@ -1002,6 +1028,8 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&unf_blocks, batch_unfold_kernel, 128, 0);
         if (unf_blocks < 1) unf_blocks = 1;
     }
+    e = cudaMemsetAsync(a.order_cnt, 0, 32 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
     batch_unfold_kernel<<<sms * unf_blocks, 128, 0, s>>>(a);
     switch (a.chunk) {
         case 8: batch_refine_kernel<8><<<grid, block, 0, s>>>(a); break;

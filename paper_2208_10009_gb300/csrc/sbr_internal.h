@@ -165,6 +165,8 @@ struct sbr_paths {
     sbr::RecDev *recs = nullptr;
     sbr_path_record *paths = nullptr;
     float4 *unf = nullptr;                 // batched refinement: each path's unfolded planes (9 float4)
+    int *order_idx = nullptr;              // batched refinement: path indices grouped by order
+    unsigned long long *order_cnt = nullptr;   // [0, 10): paths per group, [16, 26): fill cursors
     unsigned long long *table = nullptr;   // dedup hash table: 2 x u64 per slot (key, value)
     int64_t table_slots = 0;
     long long *counters = nullptr;         // sbr::kNumCounters
@@ -283,6 +285,8 @@ struct RefineArgs {
     double ptx_dbm;
     int8_t *choice_log;
     float4 *unf;              // per path: FP32 unfolded planes and W (9 float4), batched form
+    int *order_idx;           // batched form: path indices grouped by order (diffraction last)
+    unsigned long long *order_cnt;   // batched form: group sizes [0, 10) and fill cursors [16, 26)
     int chunk;                // lanes per path in the batched kernel (8, 16, 32)
     long long split_min;      // batched form: from this many paths on, validity and outputs run
                               // one thread per path in a second kernel
