@@ -133,14 +133,85 @@ struct LaneRay {
     int k, prev, txi, ray;
 };
 
+// Receptions a lane buffers during one segment before its warp flushes them.  Emitting
+// each record with its own atomic on the one record counter serialises the records at
+// that counter's L2 slice (lanes are divergent inside the receiver leaves, so nothing
+// aggregates them); the flush takes one atomic per warp step instead.
+constexpr int kPend = 4;
+
+// Shared memory of a trace block: faces [kMaxOrder][block], then the pending receptions'
+// receiver ids, error angles and ray lengths, [kPend][block] each.
+size_t trace_smem(int block) { return (size_t)(kMaxOrder + 3 * kPend) * block * sizeof(int); }
+
+// The lane's pending receptions: entry i at rx[i B], err[i B], dray[i B] with B the block
+// size, err and dray stored as float bits after the kPend receiver ids.
+struct Pending {
+    int *rx;
+    int n, k;   // count; order of the segment they were received on
+    __device__ __forceinline__ int &rx_at(int i) const { return rx[i * blockDim.x]; }
+    __device__ __forceinline__ float &err_at(int i) const {
+        return *reinterpret_cast<float *>(rx + (kPend + i) * blockDim.x);
+    }
+    __device__ __forceinline__ float &dray_at(int i) const {
+        return *reinterpret_cast<float *>(rx + (2 * kPend + i) * blockDim.x);
+    }
+};
+
+__device__ __forceinline__ void write_record(const TraceArgs &a, unsigned long long slot, const LaneRay &st, int k,
+                                             int rx, float err, float dray, const int *faces_sh, int stride_sh) {
+    if ((long long)slot >= a.rec_cap) return;
+    RecDev rec;
+    rec.tx = st.txi;
+    rec.rx = rx;
+    rec.ray = st.ray;
+    rec.order = k;
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j) rec.faces[j] = j < k ? faces_sh[j * stride_sh] : -1;
+    rec.err = err;
+    rec.dray = dray;
+    rec.slot = -1;
+    rec.pad = 0;
+    int4 *dst = reinterpret_cast<int4 *>(a.recs + slot);
+    const int4 *src = reinterpret_cast<const int4 *>(&rec);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[j] = src[j];
+}
+
+// A reception past the lane's kPend pending ones (rare): its own slot, written at once.
+__device__ __noinline__ void emit_direct(const TraceArgs &a, const LaneRay &st, int rx, float err, float dray,
+                                         const int *faces_sh, int stride_sh) {
+    const unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kRecords), 1ULL);
+    write_record(a, slot, st, st.k, rx, err, dray, faces_sh, stride_sh);
+}
+
+// Whole warp: every lane's pending receptions get consecutive slots from one atomic (lane
+// order, then reception order) and are written out.
+__device__ __forceinline__ void flush_records(const TraceArgs &a, const LaneRay &st, const int *faces_sh,
+                                              int stride_sh, Pending &pd, unsigned lane) {
+    if (__ballot_sync(0xffffffffu, pd.n > 0) == 0) return;
+    int incl = pd.n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += t;
+    }
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kRecords), (unsigned long long)incl);
+    base = __shfl_sync(0xffffffffu, base, 31) + (unsigned long long)(incl - pd.n);
+    for (int i = 0; i < pd.n; ++i)
+        write_record(a, base + i, st, pd.k, pd.rx_at(i), pd.err_at(i), pd.dray_at(i), faces_sh, stride_sh);
+    pd.n = 0;
+}
+
 // Reception judgment on segment o + s d, s in [0, tseg], of a ray that has travelled L
 // metres before it: every Rx whose foot lies on the segment and whose error angle
 // (Eq. 3) is within the cone emits a record.  Candidates come from the receivers' 4-wide
 // BVH, each box grown by the cone radius at the segment's far end; the growth is folded
 // into the per-segment slab offsets (near: o/d + rad/|d|, far: o/d - rad/|d|), so a grown
-// box costs what a plain one does.
+// box costs what a plain one does.  Receptions go to the lane's pending buffer (past
+// kPend in one segment, straight to the record array with their own atomic).
 __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, const LaneRay &st, float tseg,
-                                          const int *faces_sh, int stride_sh, unsigned &rx_tests) {
+                                          const int *faces_sh, int stride_sh, Pending &pd, unsigned &rx_tests) {
     const RxDev &R = a.rx;
     if (R.nrx == 0) return;
     float tcap = fminf(tseg, max_foot(R, st.o, st.d));
@@ -198,23 +269,13 @@ __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, c
                 float dray = st.L + s;
                 float err = atan2f(dperp, dray);
                 if (!(err <= a.cone)) continue;
-                unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kRecords), 1ULL);
-                if ((long long)slot < a.rec_cap) {
-                    RecDev rec;
-                    rec.tx = st.txi;
-                    rec.rx = __float_as_int(p.w);
-                    rec.ray = st.ray;
-                    rec.order = st.k;
-#pragma unroll
-                    for (int j = 0; j < kMaxOrder; ++j) rec.faces[j] = j < st.k ? faces_sh[j * stride_sh] : -1;
-                    rec.err = err;
-                    rec.dray = dray;
-                    rec.slot = -1;
-                    rec.pad = 0;
-                    int4 *dst = reinterpret_cast<int4 *>(a.recs + slot);
-                    const int4 *src = reinterpret_cast<const int4 *>(&rec);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) dst[j] = src[j];
+                if (pd.n < kPend) {
+                    pd.rx_at(pd.n) = __float_as_int(p.w);
+                    pd.err_at(pd.n) = err;
+                    pd.dray_at(pd.n) = dray;
+                    ++pd.n;
+                } else {
+                    emit_direct(a, st, __float_as_int(p.w), err, dray, faces_sh, stride_sh);
                 }
             }
         }
@@ -227,11 +288,15 @@ __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, c
 // least refill_min lanes hold a finished ray (miss or order cap), those lanes take fresh,
 // consecutive ray ids from a global counter with one warp-aggregated atomic (ballot +
 // popc).  Waiting for several idle lanes keeps a warp's rays neighbours in the lattice
-// (coherent traversal) while still keeping warps mostly full until the pool drains.
+// (coherent traversal) while still keeping warps mostly full until the pool drains.  After
+// every segment step the warp writes out its lanes' receptions together (flush_records).
 __global__ void __launch_bounds__(128, 8) trace_kernel(TraceArgs a) {
-    extern __shared__ int faces_sh_all[];                // [kMaxOrder][blockDim.x]
+    extern __shared__ int faces_sh_all[];   // trace_smem(blockDim.x) bytes
     int *faces_sh = faces_sh_all + threadIdx.x;
     const int stride_sh = blockDim.x;
+    Pending pd;
+    pd.rx = faces_sh_all + kMaxOrder * blockDim.x + threadIdx.x;
+    pd.n = 0;
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const long long total = (long long)a.ntx * a.nrays_per_tx;
@@ -269,30 +334,34 @@ __global__ void __launch_bounds__(128, 8) trace_kernel(TraceArgs a) {
             }
         }
         if (__ballot_sync(0xffffffffu, alive) == 0) break;
-        if (!alive) continue;
-        RayPre r = make_ray(st.o, st.d);
-        float th;
-        int face;
-        int hit = closest_hit4(a.scene, r, a.scene.tmin, INFINITY, st.prev, th, face, nodes, tris);
-        ++seg;
-        if (a.dump_stride > 0 && st.ray % a.dump_stride == 0)
-            a.dump_faces[((size_t)st.txi * a.dump_per_tx + st.ray / a.dump_stride) * (a.max_order + 1) + st.k] =
-                hit >= 0 ? face : -1;
-        float tseg = hit >= 0 ? th : INFINITY;
-        reception(a, r, st, tseg, faces_sh, stride_sh, rxt);
-        if (hit < 0 || st.k == a.max_order) {
-            alive = false;
-            continue;
+        if (alive) {
+            RayPre r = make_ray(st.o, st.d);
+            float th;
+            int face;
+            const int hit = closest_hit4(a.scene, r, a.scene.tmin, INFINITY, st.prev, th, face, nodes, tris);
+            ++seg;
+            if (a.dump_stride > 0 && st.ray % a.dump_stride == 0)
+                a.dump_faces[((size_t)st.txi * a.dump_per_tx + st.ray / a.dump_stride) * (a.max_order + 1) + st.k] =
+                    hit >= 0 ? face : -1;
+            float tseg = hit >= 0 ? th : INFINITY;
+            pd.k = st.k;
+            reception(a, r, st, tseg, faces_sh, stride_sh, pd, rxt);
+            if (hit < 0 || st.k == a.max_order) {
+                alive = false;
+            } else {
+                // specular reflection on the hit face's plane (faces_sh[j], j < pd.k, stay
+                // as the pending receptions need them)
+                float4 pl = __ldg(a.scene.planes + face);
+                float3 nrm = f3(pl);
+                st.o = st.o + st.d * th;
+                st.d = st.d - nrm * (2.0f * dot(st.d, nrm));
+                st.L += th;
+                faces_sh[st.k * stride_sh] = face;
+                st.prev = face;
+                ++st.k;
+            }
         }
-        // specular reflection on the hit face's plane
-        float4 pl = __ldg(a.scene.planes + face);
-        float3 nrm = f3(pl);
-        st.o = st.o + st.d * th;
-        st.d = st.d - nrm * (2.0f * dot(st.d, nrm));
-        st.L += th;
-        faces_sh[st.k * stride_sh] = face;
-        st.prev = face;
-        ++st.k;
+        flush_records(a, st, faces_sh, stride_sh, pd, lane);
     }
     // one atomic per warp per counter
     unsigned s0 = __reduce_add_sync(0xffffffffu, seg), s1 = __reduce_add_sync(0xffffffffu, nodes);
@@ -307,12 +376,12 @@ __global__ void __launch_bounds__(128, 8) trace_kernel(TraceArgs a) {
 
 int trace_blocks_per_sm(int block) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel, block, (size_t)kMaxOrder * block * sizeof(int));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, trace_kernel, block, trace_smem(block));
     return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_trace(const TraceArgs &a, int grid, int block, cudaStream_t s) {
-    trace_kernel<<<grid, block, (size_t)kMaxOrder * block * sizeof(int), s>>>(a);
+    trace_kernel<<<grid, block, trace_smem(block), s>>>(a);
     return cudaGetLastError();
 }
 
