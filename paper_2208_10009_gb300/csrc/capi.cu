@@ -614,7 +614,7 @@ sbr_status sbr_paths_create(sbr_ctx *ctx, int64_t record_cap, int64_t path_cap, 
     Carver cv;
     cv.add(&p->recs, (size_t)record_cap);
     cv.add(&p->paths, (size_t)path_cap);
-    cv.add(&p->unf, (size_t)path_cap * 9);
+    cv.add(&p->unf, (size_t)path_cap * kUnfStride);
     cv.add(&p->order_idx, (size_t)path_cap);
     cv.add(&p->order_cnt, (size_t)32);
     cv.add(&table, (size_t)slots * 2 + (size_t)(slots + 1) / 2);   // keys, values, winner ids
@@ -825,6 +825,10 @@ static sbr_status refine_args(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *p
     A.tan2_target = prm->target_err_rad >= 1.5707963267948966 ? INFINITY
                                                                : std::pow(std::tan(prm->target_err_rad), 2.0);
     A.fp64_below = prm->fp64_below_rad > 0 ? prm->fp64_below_rad : 1e-5;
+    A.tan2_target_f = (float)A.tan2_target;
+    A.target_on = A.target > 0.0;
+    A.fp64_below_f = (float)A.fp64_below;
+    if ((double)A.fp64_below_f < A.fp64_below) A.fp64_below_f = std::nextafter(A.fp64_below_f, INFINITY);
     A.freq = prm->freq_hz > 0 ? prm->freq_hz : 2.4e9;
     A.ptx_dbm = prm->ptx_dbm;
     A.choice_log = prm->choice_log;

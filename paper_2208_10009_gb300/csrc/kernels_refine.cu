@@ -19,6 +19,7 @@ struct SubTab {
     float rho[38], cphi[38], sphi[38];
     double rho_d[38], cphi_d[38], sphi_d[38];
     double shrink[17];
+    float shrink_f[17];          // the FP32 phase's factor: its cone radius is kept in FP32
 };
 __constant__ SubTab c_sub;
 
@@ -32,6 +33,7 @@ cudaError_t upload_subray_table(cudaStream_t s) {
         int K = subray_pattern(Ks[q], rho, phi, &sh);
         t.off[Ks[q]] = at;
         t.shrink[Ks[q]] = sh;
+        t.shrink_f[Ks[q]] = (float)sh;
         for (int k = 0; k < K; ++k, ++at) {
             t.rho[at] = (float)rho[k];
             t.cphi[at] = (float)cos(phi[k]);
@@ -239,7 +241,7 @@ __device__ __forceinline__ bool stalled(double key, double dw, double R, double 
 }
 
 __device__ __forceinline__ bool reached32(const RefineArgs &A, float key, float dw) {
-    return A.target > 0.0 && key < INFINITY && key <= dw * dw * (float)A.tan2_target;
+    return A.target_on && key < INFINITY && key <= dw * dw * A.tan2_target_f;
 }
 
 __device__ __forceinline__ bool stalled32(float key, float dw, float Rf, float stall) {
@@ -248,9 +250,18 @@ __device__ __forceinline__ bool stalled32(float key, float dw, float Rf, float s
 }
 
 // Eq. 3 error angle from key and d . W, in the precision of the phase that produced them
-__device__ __forceinline__ double error_angle(double key, double dw, bool fp64) {
-    if (!(key < INFINITY)) return INFINITY;
-    return fp64 ? atan2(sqrt(key), dw) : (double)atan2f(sqrtf((float)key), (float)dw);
+__device__ __forceinline__ double error_angle(double key, double dw, float keyf, float dwf, bool fp64) {
+    if (fp64) return key < INFINITY ? atan2(sqrt(key), dw) : INFINITY;
+    return keyf < INFINITY ? (double)atan2f(sqrtf(keyf), dwf) : INFINITY;
+}
+
+// The cone radius R0 s^it of the FP64 phase: R0 = max(theta_launch, rough error), shrunk
+// once per iteration in FP64.  (The FP32 phase keeps its own radius in FP32: on GB300
+// every FP64 instruction, conversions and compares included, costs 64 times an FP32 one.)
+__device__ __forceinline__ double cone_radius64(const RefineArgs &A, float rough_err, int it, double shrink) {
+    double R = fmax((double)A.theta_launch, (double)rough_err);
+    for (int i = 0; i < it; ++i) R *= shrink;
+    return R;
 }
 
 // sin and cos of a small angle (|x| <= 1e-3) from their Taylor series; the first omitted
@@ -574,6 +585,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
     const long long total = A.range ? (long long)(A.range[1] - A.range[0]) : path_count(A);
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
+    const float shrinkf = c_sub.shrink_f[A.K];
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
     const float stallf = (float)stall;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -590,55 +602,61 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
         UnfD ud;
         UnfF uf;
         build_unf(A.scene, g, ud, uf);
-        dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
-        double R = fmax((double)A.theta_launch, (double)p.rough_err);
-        bool fp64 = R < A.fp64_below, fail = false;
-        double key = INFINITY, dw = 0.0;
+        // FP32 phase while the cone radius is >= fp64_below (the radius R0 = max(theta_launch,
+        // rough error) is a float, so the first test is exact)
+        float Rf = fmaxf(A.theta_launch, p.rough_err);
+        bool fp64 = Rf < A.fp64_below_f, fail = false;
+        float3 cf = make_float3((float)p.dir[0], (float)p.dir[1], (float)p.dir[2]);
+        float keyf = INFINITY, dwf = 0.0f;
         int it = 0, flags = 0;
         if (!fp64) {
-            float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
-            float dwf = 0.0f, Rf = (float)R;
-            float keyf = key32(uf, g.k, cf, dwf);
+            keyf = key32(uf, g.k, cf, dwf);
             while (it < A.max_iters && !reached32(A, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
-                   !(R < A.fp64_below)) {
+                   !(Rf < A.fp64_below_f)) {
                 const int bk = iterate32(uf, g.k, A.K, off, Rf, cf, keyf, dwf);
                 if (bk < 0) {
                     fail = true;
                     break;
                 }
                 if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
-                R *= shrink;
-                Rf = (float)R;
+                Rf *= shrinkf;
                 ++it;
             }
-            c = dv(cf.x, cf.y, cf.z);
-            key = keyf;
-            dw = dwf;
-        } else {
-            key = key64(ud, g.k, c, dw);
         }
-        while (!fail && R < A.fp64_below && it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
-            const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
-            if (bk < 0) {
-                fail = true;
-                break;
+        dvec3 c = dv(cf.x, cf.y, cf.z);
+        double key = INFINITY, dw = 0.0;
+        if (!fail && Rf < A.fp64_below_f) {
+            double R = cone_radius64(A, p.rough_err, it, shrink);
+            if (fp64) {
+                c = dv(p.dir[0], p.dir[1], p.dir[2]);
+                key = key64(ud, g.k, c, dw);
+            } else {
+                key = keyf;
+                dw = dwf;
             }
-            flags |= SBR_PATH_FP64;
-            fp64 = true;
-            if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
-            R *= shrink;
-            ++it;
+            while (it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
+                const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
+                if (bk < 0) {
+                    fail = true;
+                    break;
+                }
+                flags |= SBR_PATH_FP64;
+                fp64 = true;
+                if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+                R *= shrink;
+                ++it;
+            }
         }
         if (fail) flags |= SBR_PATH_TRACE_FAIL;
-        else if (it < A.max_iters && !(fp64 ? reached(A, key, dw) : reached32(A, (float)key, (float)dw)))
+        else if (it < A.max_iters && !(fp64 ? reached(A, key, dw) : reached32(A, keyf, dwf)))
             flags |= SBR_PATH_STALLED;
         p.iters = it;
         p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
         p.dir[0] = c.x;
         p.dir[1] = c.y;
         p.dir[2] = c.z;
-        p.err = error_angle(key, dw, fp64);
-        finalize_path(A, g, c, p, converged_bound(it, R));
+        p.err = error_angle(key, dw, keyf, dwf, fp64);
+        finalize_path(A, g, c, p, converged_bound(it, cone_radius64(A, p.rough_err, it, shrink)));
         store_result(A.paths + pi, p);
     }
 }
@@ -811,6 +829,7 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
     const bool prebuilt = total >= A.split_min;   // batch_unfold_kernel ran
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
+    const float shrinkf = c_sub.shrink_f[A.K];
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
     const float stallf = (float)stall;
     const int lane = threadIdx.x & 31;
@@ -837,70 +856,78 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
         // lanes 0..k-1 (one plane each) and lane G-1 (the receiver; k <= 8 <= G).  The
         // previous path's data is no longer read once every lane has reached this point.
         __syncwarp(gmask);
+        float3 cf;
         if (prebuilt) {
             for (int j = gl; j <= kMaxOrder; j += G)
-                if (j < g.k || j == kMaxOrder) (j < kMaxOrder ? uf.p[j] : uf.w) = A.unf[9 * pi + j];
+                if (j < g.k || j == kMaxOrder) (j < kMaxOrder ? uf.p[j] : uf.w) = A.unf[kUnfStride * pi + j];
+            cf = f3(A.unf[kUnfStride * pi + kMaxOrder + 1]);
         } else {
             if (gl < g.k) set_unf(ud, uf, gl, unfold_plane(A.scene, g, gl));
             if (gl == G - 1) set_unf(ud, uf, kMaxOrder, unfold_rx(A.scene, g));
+            cf = make_float3((float)p.dir[0], (float)p.dir[1], (float)p.dir[2]);
         }
         __syncwarp(gmask);
-        dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
-        double R = fmax((double)A.theta_launch, (double)p.rough_err);
-        bool fp64 = R < A.fp64_below, fail = false;
-        double key = INFINITY, dw = 0.0;
+        // FP32 phase, every operand in FP32 (see cone_radius64); state identical in the G lanes
+        float Rf = fmaxf(A.theta_launch, p.rough_err);
+        bool fp64 = Rf < A.fp64_below_f, fail = false;
+        float keyf = INFINITY, dwf = 0.0f;
         int it = 0, flags = 0;
         if (!fp64) {
-            float3 cf = make_float3((float)c.x, (float)c.y, (float)c.z);
-            float dwf = 0.0f, Rf = (float)R;
-            float keyf = key32(uf, g.k, cf, dwf);
+            keyf = key32(uf, g.k, cf, dwf);
             while (it < A.max_iters && !reached32(A, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
-                   !(R < A.fp64_below)) {
+                   !(Rf < A.fp64_below_f)) {
                 const int bk = group_iterate32<G>(uf, g.k, A.K, off, Rf, cf, keyf, dwf, gl, gmask);
                 if (bk < 0) {
                     fail = true;
                     break;
                 }
                 if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
-                R *= shrink;
-                Rf = (float)R;
+                Rf *= shrinkf;
                 ++it;
             }
-            c = dv(cf.x, cf.y, cf.z);
-            key = keyf;
-            dw = dwf;
         }
-        if (!fail && R < A.fp64_below) {
+        dvec3 c;
+        double key = INFINITY, dw = 0.0;
+        if (!fail && Rf < A.fp64_below_f) {
             // the FP64 phase needs the FP64 planes: built here if only the FP32 copy was read
             if (prebuilt) {
                 if (gl < g.k) ud.p[gl] = unfold_plane(A.scene, g, gl);
                 if (gl == G - 1) ud.w = unfold_rx(A.scene, g);
                 __syncwarp(gmask);
             }
-            if (fp64) key = key64(ud, g.k, c, dw);
-        }
-        while (!fail && R < A.fp64_below && it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
-            const int bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
-            if (bk < 0) {
-                fail = true;
-                break;
+            double R = cone_radius64(A, p.rough_err, it, shrink);
+            if (fp64) {
+                c = dv(p.dir[0], p.dir[1], p.dir[2]);
+                key = key64(ud, g.k, c, dw);
+            } else {
+                c = dv(cf.x, cf.y, cf.z);
+                key = keyf;
+                dw = dwf;
             }
-            flags |= SBR_PATH_FP64;
-            fp64 = true;
-            if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
-            R *= shrink;
-            ++it;
+            while (it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
+                const int bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
+                if (bk < 0) {
+                    fail = true;
+                    break;
+                }
+                flags |= SBR_PATH_FP64;
+                fp64 = true;
+                if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+                R *= shrink;
+                ++it;
+            }
         }
         if (fail) flags |= SBR_PATH_TRACE_FAIL;
-        else if (it < A.max_iters && !(fp64 ? reached(A, key, dw) : reached32(A, (float)key, (float)dw)))
+        else if (it < A.max_iters && !(fp64 ? reached(A, key, dw) : reached32(A, keyf, dwf)))
             flags |= SBR_PATH_STALLED;
-        p.iters = it;
-        p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
-        p.dir[0] = c.x;
-        p.dir[1] = c.y;
-        p.dir[2] = c.z;
-        p.err = error_angle(key, dw, fp64);
         if (gl == 0) {
+            if (!fp64) c = dv(cf.x, cf.y, cf.z);
+            p.iters = it;
+            p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
+            p.dir[0] = c.x;
+            p.dir[1] = c.y;
+            p.dir[2] = c.z;
+            p.err = error_angle(key, dw, keyf, dwf, fp64);
             if (prebuilt) {
                 // list the path in its order group (group offsets from batch_unfold_kernel's
                 // counts), so that the finalize kernel's warps see paths of one order
@@ -925,7 +952,7 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
 // Batched form, first pass (from split_min paths on), one thread per path: the FP64
 // unfolding of the path's face planes into Tx's space and of the receiver (the same
 // arithmetic as the plain form's build_unf), stored rounded to FP32 for the iteration
-// kernel.  GB300 runs FP64 at 1/64 of
+// kernel, with the rough launch direction rounded to FP32.  GB300 runs FP64 at 1/64 of
 // the FP32 rate; with one path per lane every FP64 instruction serves 32 paths, where the
 // iteration kernel's lane groups would serve one.
 // It also counts the paths of each order group so that the iteration kernel can list them
@@ -943,12 +970,14 @@ __global__ void __launch_bounds__(128) batch_unfold_kernel(RefineArgs A) {
         PathGeo g;
         load_path(A, p, g);
         atomicAdd(&hist[order_group(g)], 1u);
+        float4 *u = A.unf + kUnfStride * pi;
         for (int j = 0; j < g.k; ++j) {
             const D4 P = unfold_plane(A.scene, g, j);
-            A.unf[9 * pi + j] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)P.w);
+            u[j] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)P.w);
         }
         const D4 W = unfold_rx(A.scene, g);
-        A.unf[9 * pi + kMaxOrder] = make_float4((float)W.x, (float)W.y, (float)W.z, (float)W.w);
+        u[kMaxOrder] = make_float4((float)W.x, (float)W.y, (float)W.z, (float)W.w);
+        u[kMaxOrder + 1] = make_float4((float)p.dir[0], (float)p.dir[1], (float)p.dir[2], 0.0f);
     }
     __syncthreads();
     if (threadIdx.x < 10 && hist[threadIdx.x]) atomicAdd(A.order_cnt + threadIdx.x, (unsigned long long)hist[threadIdx.x]);
@@ -978,8 +1007,7 @@ __global__ void __launch_bounds__(128) batch_finalize_kernel(RefineArgs A) {
         if (!path_ids_ok(A, p)) continue;   // already flagged by the iteration kernel
         PathGeo g;
         load_path(A, p, g);
-        double R = fmax((double)A.theta_launch, (double)p.rough_err);
-        for (int i = 0; i < p.iters; ++i) R *= shrink;
+        const double R = cone_radius64(A, p.rough_err, p.iters, shrink);
         dvec3 c = dv(p.dir[0], p.dir[1], p.dir[2]);
         if (per_thread) {
             finalize_path(A, g, c, p, converged_bound(p.iters, R));

@@ -13,6 +13,7 @@
 namespace sbr {
 
 constexpr int kMaxOrder = SBR_MAX_ORDER;
+constexpr int kUnfStride = kMaxOrder + 2;   // float4 per path in the batched refinement's unf
 constexpr double kC0 = 299792458.0;
 constexpr int kLeafMax = 2;        // triangles per BVH leaf (target; 2 measured fastest: a
                                    // triangle test costs about half a 4-wide node visit)
@@ -164,7 +165,7 @@ struct sbr_paths {
     size_t bytes = 0;
     sbr::RecDev *recs = nullptr;
     sbr_path_record *paths = nullptr;
-    float4 *unf = nullptr;                 // batched refinement: each path's unfolded planes (9 float4)
+    float4 *unf = nullptr;                 // batched refinement: kUnfStride float4 per path
     int *order_idx = nullptr;              // batched refinement: path indices grouped by order
     unsigned long long *order_cnt = nullptr;   // [0, 10): paths per group, [16, 26): fill cursors
     unsigned long long *table = nullptr;   // dedup hash table: 2 x u64 per slot (key, value)
@@ -280,11 +281,16 @@ struct RefineArgs {
     float theta_launch;
     double target;
     double tan2_target;       // tan^2(target) (early-stop test on |d x W|^2)
+    float tan2_target_f;      // (float)tan2_target, for the FP32 phase
+    int target_on;            // target > 0
     double fp64_below;
+    float fp64_below_f;       // smallest float >= fp64_below: for a float x,
+                              // x < fp64_below_f  <=>  x < fp64_below
     double freq;
     double ptx_dbm;
     int8_t *choice_log;
-    float4 *unf;              // per path: FP32 unfolded planes and W (9 float4), batched form
+    float4 *unf;              // batched form, per path (kUnfStride float4): FP32 unfolded planes
+                              // [0, kMaxOrder), W at kMaxOrder, rough direction at kMaxOrder + 1
     int *order_idx;           // batched form: path indices grouped by order (diffraction last)
     unsigned long long *order_cnt;   // batched form: group sizes [0, 10) and fill cursors [16, 26)
     int chunk;                // lanes per path in the batched kernel (8, 16, 32)
