@@ -698,6 +698,7 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     double cone = prm->rx_angle_scale * sbr_theta_launch(prm->n_div);
     a.cone = (float)cone;
     a.tan_cone = (float)std::tan(cone);
+    a.tan2_pre = cone < 1.5 ? (float)(std::tan(cone) * std::tan(cone) * (1.0 + 1e-4)) : INFINITY;
     a.recs = paths->recs;
     a.rec_cap = paths->record_cap;
     a.counters = paths->counters;

@@ -136,25 +136,24 @@ struct LaneRay {
 // Receptions a lane buffers during one segment before its warp flushes them.  Emitting
 // each record with its own atomic on the one record counter serialises the records at
 // that counter's L2 slice (lanes are divergent inside the receiver leaves, so nothing
-// aggregates them); the flush takes one atomic per warp step instead.
-constexpr int kPend = 4;
+// aggregates them); the flush takes one atomic per warp step instead.  The buffer is a
+// per-thread array in local memory (L1-cached); a segment can see many receivers when
+// the cone has grown wide, so it holds kPend of them, and any further ones take their
+// own slot at once.
+constexpr int kPend = 16;
 
-// Shared memory of a trace block: faces [kMaxOrder][block], then the pending receptions'
-// receiver ids, error angles and ray lengths, [kPend][block] each.
-size_t trace_smem(int block) { return (size_t)(kMaxOrder + 3 * kPend) * block * sizeof(int); }
+// Shared memory of a trace block: the faces of each thread's ray, [kMaxOrder][block].
+size_t trace_smem(int block) { return (size_t)kMaxOrder * block * sizeof(int); }
 
-// The lane's pending receptions: entry i at rx[i B], err[i B], dray[i B] with B the block
-// size, err and dray stored as float bits after the kPend receiver ids.
+// The lane's pending receptions: receiver id, error angle and ray length of each (arrays
+// in the thread's local memory), their count and the order of their segment (registers).
 struct Pending {
     int *rx;
-    int n, k;   // count; order of the segment they were received on
-    __device__ __forceinline__ int &rx_at(int i) const { return rx[i * blockDim.x]; }
-    __device__ __forceinline__ float &err_at(int i) const {
-        return *reinterpret_cast<float *>(rx + (kPend + i) * blockDim.x);
-    }
-    __device__ __forceinline__ float &dray_at(int i) const {
-        return *reinterpret_cast<float *>(rx + (2 * kPend + i) * blockDim.x);
-    }
+    float *err, *dray;
+    int n, k;
+    __device__ __forceinline__ int &rx_at(int i) { return rx[i]; }
+    __device__ __forceinline__ float &err_at(int i) { return err[i]; }
+    __device__ __forceinline__ float &dray_at(int i) { return dray[i]; }
 };
 
 __device__ __forceinline__ void write_record(const TraceArgs &a, unsigned long long slot, const LaneRay &st, int k,
@@ -265,9 +264,11 @@ __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, c
                 float s = dot(w, st.d);
                 if (s < 0.0f || s > tseg) continue;
                 float3 q = w - st.d * s;
-                float dperp = sqrtf(dot(q, q));
-                float dray = st.L + s;
-                float err = atan2f(dperp, dray);
+                const float q2 = dot(q, q), dray = st.L + s;
+                // far outside the cone (a margin of 1e-4 on tan^2 dwarfs the FP32 rounding):
+                // rejected without the square root and arc tangent of the exact test
+                if (q2 > a.tan2_pre * dray * dray) continue;
+                float err = atan2f(sqrtf(q2), dray);
                 if (!(err <= a.cone)) continue;
                 if (pd.n < kPend) {
                     pd.rx_at(pd.n) = __float_as_int(p.w);
@@ -294,8 +295,12 @@ __global__ void __launch_bounds__(128, 8) trace_kernel(TraceArgs a) {
     extern __shared__ int faces_sh_all[];   // trace_smem(blockDim.x) bytes
     int *faces_sh = faces_sh_all + threadIdx.x;
     const int stride_sh = blockDim.x;
+    int pend_rx[kPend];
+    float pend_err[kPend], pend_dray[kPend];
     Pending pd;
-    pd.rx = faces_sh_all + kMaxOrder * blockDim.x + threadIdx.x;
+    pd.rx = pend_rx;
+    pd.err = pend_err;
+    pd.dray = pend_dray;
     pd.n = 0;
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;

@@ -229,6 +229,8 @@ struct TraceArgs {
     int max_order;
     float cone;               // reception cone half-angle (rad)
     float tan_cone;
+    float tan2_pre;           // tan^2(cone) (1 + 1e-4): conservative pre-test |q|^2 > tan2_pre d_ray^2
+                              // rejects before the exact Eq. 3 test (INFINITY: no pre-test)
     RecDev *recs;
     int64_t rec_cap;
     long long *counters;
