@@ -361,8 +361,7 @@ __device__ __forceinline__ int iterate64(const UnfD &ud, int nk, int K, int off,
 
 // ----------------------------------------------------------------------------- a7/a8
 __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p) {
-    Plane64 pl = S.planes_d[f];
-    dvec3 n = dv(pl.x, pl.y, pl.z);
+    const float3 nf = f3(__ldg(S.planes + f));   // the FP64 normal rounded to FP32
     const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
     const float tol = 1e-6f * (fabsf(px) + fabsf(py) + fabsf(pz)) + 1e-6f;
     int stack[kStackDepth];
@@ -396,7 +395,7 @@ __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p)
                 if (__float_as_int(A.w) != f) continue;
                 // edge functions in FP32; a sign within a generous rounding bound of zero
                 // (1e-5 x |edge| x (|p| + |p - vertex| + 1), 1-norms) is decided again in FP64
-                const float3 P = make_float3(px, py, pz), nf = make_float3((float)n.x, (float)n.y, (float)n.z);
+                const float3 P = make_float3(px, py, pz);
                 const float3 ab = f3(B) - f3(A), bc = f3(C) - f3(B), ca = f3(A) - f3(C);
                 const float3 pa = P - f3(A), pb = P - f3(B), pc = P - f3(C);
                 const float ea = dot(cross(ab, pa), nf);
@@ -411,6 +410,8 @@ __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p)
                     if ((ea > 0 && eb > 0 && ec > 0) || (ea < 0 && eb < 0 && ec < 0)) return true;
                     continue;
                 }
+                const Plane64 pl = S.planes_d[f];
+                const dvec3 n = dv(pl.x, pl.y, pl.z);
                 dvec3 a = dv(A.x, A.y, A.z), b = dv(B.x, B.y, B.z), c = dv(C.x, C.y, C.z);
                 double da = ddot(dcross(b - a, p - a), n);
                 double db = ddot(dcross(c - b, p - b), n);
@@ -543,8 +544,19 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
     // Rx must be received on the last leg (its foot lies ahead of the last bounce point)
     // and the refinement must have converged
     bool valid = ddot(g.rxd - (g.k > 0 ? pts[g.k - 1] : g.txd), dl) > 0.0 && p.err <= err_bound;
-    for (int j = 0; j < g.k && valid; ++j) valid = point_in_face(S, g.faces[j], pts[j]);
-    for (int j = 0; j <= g.k && valid; ++j) {
+    // The lanes that arrive here together run the queries in lockstep: loop bounds made
+    // uniform over them, a lane that has failed a test idles through the rest, so that the
+    // lanes execute the same traversal code at the same time (a per-lane early exit would
+    // let one lane's occlusion queries run beside another's point-in-face queries).
+    const unsigned m = __activemask();
+    const int kk = __reduce_max_sync(m, g.k);
+    for (int j = 0; j < kk; ++j) {
+        if (!__any_sync(m, valid)) break;
+        if (valid && j < g.k) valid = point_in_face(S, g.faces[j], pts[j]);
+    }
+    for (int j = 0; j <= kk; ++j) {
+        if (!__any_sync(m, valid)) break;
+        if (!valid || j > g.k) continue;
         dvec3 from = j == 0 ? g.txd : pts[j - 1];
         dvec3 to = j == g.k ? g.rxd : pts[j];
         dvec3 seg = to - from;
@@ -988,7 +1000,9 @@ __global__ void __launch_bounds__(128) batch_unfold_kernel(RefineArgs A) {
 // so GB300's narrow FP64 pipe serves 32 paths per instruction.  With few paths, one warp
 // per path with the point-in-face and occlusion queries spread over its lanes (latency).
 // The cone radius after `iters` iterations is recomputed with the same multiplications.
-__global__ void __launch_bounds__(128) batch_finalize_kernel(RefineArgs A) {
+// The queries are latency-bound: eight blocks per SM (64 registers, some spilled to L1)
+// measured faster than four without spills.
+__global__ void __launch_bounds__(128, 8) batch_finalize_kernel(RefineArgs A) {
     __shared__ UnfD s_sh[4];
     const long long total = path_count(A);
     const double shrink = c_sub.shrink[A.K];
