@@ -393,8 +393,10 @@ __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p)
                 const float4 *t = S.tris + 3 * (size_t)i;
                 float4 A = __ldg(t), B = __ldg(t + 1), C = __ldg(t + 2);
                 if (__float_as_int(A.w) != f) continue;
-                // edge functions in FP32; a sign within a generous rounding bound of zero
-                // (1e-5 x |edge| x (|p| + |p - vertex| + 1), 1-norms) is decided again in FP64
+                // edge functions in FP32; a sign outside a generous rounding bound of zero
+                // (1e-5 x |edge| x (|p| + |p - vertex| + 1), 1-norms) is the FP64 sign.  Two
+                // such signs that differ put p outside; three that agree put it inside; any
+                // other case is decided in FP64.
                 const float3 P = make_float3(px, py, pz);
                 const float3 ab = f3(B) - f3(A), bc = f3(C) - f3(B), ca = f3(A) - f3(C);
                 const float3 pa = P - f3(A), pb = P - f3(B), pc = P - f3(C);
@@ -405,11 +407,11 @@ __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p)
                 auto bound = [&](float3 e, float3 q) {
                     return 1e-5f * sqrtf(dot(e, e)) * (pn + fabsf(q.x) + fabsf(q.y) + fabsf(q.z));
                 };
-                const bool sure = fabsf(ea) > bound(ab, pa) && fabsf(eb) > bound(bc, pb) && fabsf(ec) > bound(ca, pc);
-                if (sure) {
-                    if ((ea > 0 && eb > 0 && ec > 0) || (ea < 0 && eb < 0 && ec < 0)) return true;
-                    continue;
-                }
+                const bool sa = fabsf(ea) > bound(ab, pa), sb = fabsf(eb) > bound(bc, pb), sc = fabsf(ec) > bound(ca, pc);
+                const bool pos = (sa && ea > 0.0f) || (sb && eb > 0.0f) || (sc && ec > 0.0f);
+                const bool neg = (sa && ea < 0.0f) || (sb && eb < 0.0f) || (sc && ec < 0.0f);
+                if (pos && neg) continue;
+                if (sa && sb && sc) return true;
                 const Plane64 pl = S.planes_d[f];
                 const dvec3 n = dv(pl.x, pl.y, pl.z);
                 dvec3 a = dv(A.x, A.y, A.z), b = dv(B.x, B.y, B.z), c = dv(C.x, C.y, C.z);
