@@ -441,11 +441,13 @@ __device__ __forceinline__ void az_el(dvec3 v, float *out) {
 }
 
 // Bounce points p_j of launch direction c through the path's fixed planes (FP64), with
-// den_j = n_j . d_j (the incidence cosine up to sign) and the direction of the last leg.
-// Returns false if a segment length is not positive.
+// den_j = n_j . d_j (the incidence cosine up to sign), the direction of the last leg and
+// the sum of the segment parameters t_j (each leg is t_j d_j with |d_j| = |c|: mirroring
+// keeps the length).  Returns false if a segment length is not positive.
 __device__ __forceinline__ bool trace_bounces(const SceneDev &S, const PathGeo &g, dvec3 c, dvec3 *pts,
-                                              double *dens, dvec3 &d_last) {
+                                              double *dens, dvec3 &d_last, double &tsum) {
     dvec3 o = g.txd, d = c;
+    tsum = 0.0;
 #pragma unroll
     for (int j = 0; j < kMaxOrder; ++j) {
         if (j >= g.k) break;
@@ -454,6 +456,7 @@ __device__ __forceinline__ bool trace_bounces(const SceneDev &S, const PathGeo &
         double den = ddot(n, d);
         double t = den != 0.0 ? (pl.w - ddot(n, o)) / den : -1.0;
         if (!(t > 0.0)) return false;
+        tsum += t;
         o = o + d * t;
         pts[j] = o;
         dens[j] = den;
@@ -463,16 +466,13 @@ __device__ __forceinline__ bool trace_bounces(const SceneDev &S, const PathGeo &
     return true;
 }
 
-// a8 outputs of a traced path: delay = polyline length (FP64) / c0; AOD, AOA and power =
-// ptx + free-space loss + Fresnel reflection losses in FP32, as the record stores them
+// a8 outputs of a traced path: delay = polyline length (FP64) / c0, the legs up to the
+// last bounce point as |c| sum t_j, the last one to Rx from its end points; AOD, AOA and
+// power = ptx + free-space loss + Fresnel reflection losses in FP32, as the record stores
+// them
 __device__ __forceinline__ void path_outputs(const RefineArgs &A, const PathGeo &g, dvec3 c, const dvec3 *pts,
-                                             const double *dens, sbr_path_record &p) {
-    double len = 0.0;
-    for (int j = 0; j <= g.k; ++j) {
-        dvec3 from = j == 0 ? g.txd : pts[j - 1];
-        dvec3 to = j == g.k ? g.rxd : pts[j];
-        len += dnorm(to - from);
-    }
+                                             const double *dens, double tsum, sbr_path_record &p) {
+    const double len = (g.k > 0 ? tsum * dnorm(c) : 0.0) + dnorm(g.rxd - (g.k > 0 ? pts[g.k - 1] : g.txd));
     float gain_db = 0.0f;
     for (int j = 0; j < g.k; ++j) {
         float eps = __ldg(A.scene.face_eps + g.faces[j]);
@@ -537,7 +537,8 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
     dvec3 pts[kMaxOrder];
     double dens[kMaxOrder];
     dvec3 dl = c;
-    if (!trace_bounces(S, g, c, pts, dens, dl)) {
+    double tsum;
+    if (!trace_bounces(S, g, c, pts, dens, dl, tsum)) {
         p.valid = 0;
         p.flags |= SBR_PATH_TRACE_FAIL;
         p.delay = 0.0;
@@ -569,7 +570,7 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
         if (any_hit4(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) valid = false;
     }
     p.valid = valid ? 1 : 0;
-    path_outputs(A, g, c, pts, dens, p);
+    path_outputs(A, g, c, pts, dens, tsum, p);
 }
 
 __device__ __forceinline__ void store_result(sbr_path_record *dst, const sbr_path_record &p) {
@@ -774,7 +775,8 @@ __device__ __forceinline__ int group_iterate64(const UnfD &ud, int nk, int K, in
 
 // Validity and outputs with the per-bounce / per-segment queries spread over the group.
 // Lane 0 traces the bounce points once (FP64) and shares them through the group's slot
-// of shared memory (sh.p[j] = (p_j, den_j), sh.w = (direction of the last leg, ok)).
+// of shared memory (sh.p[j] = (p_j, den_j), sh.w = (direction of the last leg, sum of
+// the segment parameters, or -1 if the trace failed)).
 template <int G>
 __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, sbr_path_record &p, int gl,
                                unsigned gmask, double err_bound, UnfD &sh) {
@@ -788,12 +790,13 @@ __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
         dvec3 pts[kMaxOrder];
         double dens[kMaxOrder];
         dvec3 dl = c;
-        bool ok = trace_bounces(S, g, c, pts, dens, dl);
+        double tsum;
+        bool ok = trace_bounces(S, g, c, pts, dens, dl, tsum);
         for (int j = 0; j < g.k; ++j) sh.p[j] = {pts[j].x, pts[j].y, pts[j].z, dens[j]};
-        sh.w = {dl.x, dl.y, dl.z, ok ? 1.0 : 0.0};
+        sh.w = {dl.x, dl.y, dl.z, ok ? tsum : -1.0};
     }
     __syncwarp(gmask);
-    if (sh.w.w == 0.0) {
+    if (sh.w.w < 0.0) {
         p.valid = 0;
         p.flags |= SBR_PATH_TRACE_FAIL;
         p.delay = 0.0;
@@ -828,7 +831,7 @@ __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
             pts[j] = dv(sh.p[j].x, sh.p[j].y, sh.p[j].z);
             dens[j] = sh.p[j].w;
         }
-        path_outputs(A, g, c, pts, dens, p);
+        path_outputs(A, g, c, pts, dens, sh.w.w, p);
     }
 }
 
