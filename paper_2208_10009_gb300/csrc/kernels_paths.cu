@@ -39,15 +39,38 @@ __device__ __forceinline__ long long num_records(const DedupArgs &a) {
     return n < a.rec_cap ? n : a.rec_cap;
 }
 
+// Slots in use for this launch: the smallest power of two >= 2 n (at least 1024, at most
+// the table's), so that a launch with few records clears and probes a small table that
+// stays in L2 (the distinct keys are at most n: load factor <= 1/2).
+__device__ __forceinline__ unsigned long long used_slots(const DedupArgs &a) {
+    const long long n = num_records(a);
+    long long s = 1024;
+    while (s < 2 * n && s < a.slots) s <<= 1;
+    return (unsigned long long)(s < a.slots ? s : a.slots);
+}
+
+// keys and values to all-ones (empty / +inf), winners to -1, over the used slots
+__global__ void dedup_clear(DedupArgs a) {
+    const unsigned long long m = used_slots(a);
+    unsigned long long *keys = a.table, *vals = a.table + a.slots;
+    int *winner = reinterpret_cast<int *>(a.table + 2 * a.slots);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < m;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        keys[i] = ~0ULL;
+        vals[i] = ~0ULL;
+        winner[i] = -1;
+    }
+}
+
 __global__ void dedup_insert(DedupArgs a) {
     const long long n = num_records(a);
     unsigned long long *keys = a.table, *vals = a.table + a.slots;
-    const unsigned long long mask = (unsigned long long)a.slots - 1;
+    const unsigned long long used = used_slots(a), mask = used - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         RecDev r = a.recs[i];
         unsigned long long h = rec_hash(r), v = rec_value(r);
         unsigned long long s = h & mask;
-        for (long long probe = 0; probe < a.slots; ++probe) {
+        for (unsigned long long probe = 0; probe < used; ++probe) {
             unsigned long long prev = atomicCAS(keys + s, ~0ULL, h);
             if (prev == ~0ULL || prev == h) {
                 atomicMin(vals + s, v);
@@ -110,10 +133,8 @@ __global__ void dedup_verify(DedupArgs a) {
 }
 
 cudaError_t launch_dedup(const DedupArgs &a, int num_sms, cudaStream_t s) {
-    // keys and values start at all-ones (empty / +inf); winners at -1
-    cudaError_t e = cudaMemsetAsync(a.table, 0xFF, (size_t)a.slots * (2 * sizeof(unsigned long long) + sizeof(int)), s);
-    if (e != cudaSuccess) return e;
     int grid = num_sms * 4;
+    dedup_clear<<<grid, 256, 0, s>>>(a);
     dedup_insert<<<grid, 256, 0, s>>>(a);
     dedup_select<<<grid, 256, 0, s>>>(a);
     dedup_verify<<<grid, 256, 0, s>>>(a);

@@ -277,6 +277,19 @@ __device__ __forceinline__ void sincos_sub(double x, double &s, double &c) {
     else sincos(x, &s, &c);
 }
 
+// FP32 sine and cosine of a sub-ray's cone angle: for |x| <= 0.03 the Taylor polynomials
+// x (1 - x^2/6 + x^4/120) and 1 - x^2/2 + x^4/24 (first omitted terms below 2e-13 of the
+// result, far under FP32 rounding); wider cones use sincosf.
+__device__ __forceinline__ void sincos_sub32(float x, float &s, float &c) {
+    if (fabsf(x) <= 0.03f) {
+        const float x2 = x * x;
+        s = x * fmaf(x2, fmaf(x2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+        c = fmaf(x2, fmaf(x2, 1.0f / 24.0f, -0.5f), 1.0f);
+    } else {
+        sincosf(x, &s, &c);
+    }
+}
+
 // sub-cone frame: u = normalize(c x e), e the world axis with the smallest |c_i| (lowest
 // index on ties), v = c x u
 __device__ __forceinline__ void frame32(float3 c, float3 &u, float3 &v) {
@@ -311,7 +324,7 @@ __device__ __forceinline__ int iterate32(const UnfF &uf, int nk, int K, int off,
     float3 bd = cf;
     for (int k = 0; k < K; ++k) {
         float sa, ca;
-        sincosf(c_sub.rho[off + k] * Rf, &sa, &ca);
+        sincos_sub32(c_sub.rho[off + k] * Rf, sa, ca);
         float3 dk = cf * ca + (u * c_sub.cphi[off + k] + v * c_sub.sphi[off + k]) * sa;
         float dw = 0.0f;
         float key = key32(uf, nk, dk, dw);
@@ -718,7 +731,7 @@ __device__ __forceinline__ int group_iterate32(const UnfF &uf, int nk, int K, in
     int bk = 0x7fffffff;
     for (int k = gl; k < K; k += G) {
         float sa, ca;
-        sincosf(c_sub.rho[off + k] * Rf, &sa, &ca);
+        sincos_sub32(c_sub.rho[off + k] * Rf, sa, ca);
         float3 dk = cf * ca + (u * c_sub.cphi[off + k] + v * c_sub.sphi[off + k]) * sa;
         float dw;
         float key = key32(uf, nk, dk, dw);
@@ -731,7 +744,7 @@ __device__ __forceinline__ int group_iterate32(const UnfF &uf, int nk, int K, in
     if (!(best < INFINITY)) return -1;
     // every lane rebuilds the winning direction (same arithmetic as the lane that found it)
     float sa, ca;
-    sincosf(c_sub.rho[off + bk] * Rf, &sa, &ca);
+    sincos_sub32(c_sub.rho[off + bk] * Rf, sa, ca);
     float3 bd = cf * ca + (u * c_sub.cphi[off + bk] + v * c_sub.sphi[off + bk]) * sa;
     float dw = 0.0f;
     float key = key32(uf, nk, bd, dw);
