@@ -339,7 +339,7 @@ def run_gpu(args):
                         "traffic_source": None if traffic is None else traffic_rec.get("capture"),
                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} MEASURED_PEAKS.json)",
                         "flops_per_launch": flops},
-           "clocks": clocks, "gpu_launches": (10 if LAUNCH_OPTS["diffraction"] else 8) * args.steps,
+           "clocks": clocks, "gpu_launches": (11 if LAUNCH_OPTS["diffraction"] else 9) * args.steps,
            "wall_s": t_wall, "e2e": e2e}
     if rank == 0 and not args.no_cpu_baseline and args.workload == "canyon":
         stride = 4
