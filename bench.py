@@ -303,7 +303,8 @@ def run_gpu(args):
     sms = ctx.num_sms
     peak_tflops = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = flops / (st_t["ms_trace"] / 1e3) / 1e12
-    traffic, traffic_rec = trace_traffic()
+    # the committed ncu traffic record is of the urban-canyon launch
+    traffic, traffic_rec = trace_traffic() if args.workload == "canyon" else (None, None)
 
     # the batched graph form vs the plain per-pair launch-and-refine form
     per_pair_ms = _per_pair_ms(ctx, scene, tx_dev, rxs, paths, n, order, alpha, iters, K, len(tx), len(rx), target)
@@ -339,7 +340,7 @@ def run_gpu(args):
                         "traffic_source": None if traffic is None else traffic_rec.get("capture"),
                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} MEASURED_PEAKS.json)",
                         "flops_per_launch": flops},
-           "clocks": clocks, "gpu_launches": (11 if LAUNCH_OPTS["diffraction"] else 9) * args.steps,
+           "clocks": clocks, "gpu_launches": (12 if LAUNCH_OPTS["diffraction"] else 10) * args.steps,
            "wall_s": t_wall, "e2e": e2e}
     if rank == 0 and not args.no_cpu_baseline and args.workload == "canyon":
         stride = 4

@@ -704,6 +704,22 @@ static double trace_planes(const scene *s, vec3 tx, vec3 rx, int order, const in
     return atan2(dperp, dray);
 }
 
+static vec3 mirror(const scene *s, int f, vec3 x);
+
+/*
+ * AOA error of the path launched along d (§IV: AOA is the direction from Rx to the last
+ * bounce point p_k): the angle at Rx between p_k - Rx and the exact direction, which
+ * points at txk, Tx imaged through the k faces in order (the image method's last image
+ * lies on the straight line from Rx through the exact p_k).  Zero for LOS, whose AOA
+ * points at Tx for every launch direction; +inf if the fixed-face trace fails.
+ */
+static double aoa_error(const scene *s, vec3 tx, vec3 rx, int order, const int32_t *faces, vec3 d, vec3 txk) {
+    if (order == 0) return 0.0;
+    vec3 pts[ORA_MAX_ORDER];
+    if (!(trace_planes(s, tx, rx, order, faces, d, pts, NULL) < INFINITY)) return INFINITY;
+    return angle_between(sub(pts[order - 1], rx), sub(txk, rx));
+}
+
 /*
  * Sub-cone frame for cone centre c: u = normalize(c x e), e the world axis with the
  * smallest |c . e_i| (lowest index on ties); v = c x u.
@@ -724,7 +740,9 @@ static void cone_frame(vec3 c, vec3 *u, vec3 *v) {
  * path's fixed faces, evaluates Eq. 3 for each, keeps the sub-ray with the smallest
  * error (lowest k on ties; the parent ray does not compete) as the new centre and
  * shrinks the cone by the pattern's factor.  It stops after `iters` iterations or as
- * soon as the error is <= target (target <= 0: never early).  If every sub-ray is
+ * soon as the path meets the accuracy requirement (target <= 0: never early): the error
+ * angle, which is the AOD error, and the AOA error (aoa_error) both <= target.  If every
+ * sub-ray is
  * invalid the iteration stops.  Returns iterations done; writes the final direction, its
  * error, and per-iteration choice (argmin k) and error history (err_hist[0] = error of
  * c0).
@@ -746,12 +764,15 @@ int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const 
     double rho[16], phi[16], shrink;
     if (ora_subray_pattern(K, rho, phi, &shrink) != K) return -1;
     vec3 tx = ld(tx3), rx = ld(rx3), c = unit(ld(c0));
+    vec3 txk = tx;
+    for (int j = 0; j < order; ++j) txk = mirror(s, faces[j], txk);
     double R = R0;
     double err = trace_planes(s, tx, rx, order, faces, c, NULL, NULL);
+    double aoa = target > 0 ? aoa_error(s, tx, rx, order, faces, c, txk) : INFINITY;
     if (err_hist) err_hist[0] = err;
     int it = 0;
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
-    while (it < iters && !(target > 0 && err <= target) && !(err > R * stall + 1e-6)) {
+    while (it < iters && !(target > 0 && err <= target && aoa <= target) && !(err > R * stall + 1e-6)) {
         vec3 u, v, best_d = c;
         double best = INFINITY;
         int bk = -1;
@@ -765,6 +786,7 @@ int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const 
         if (bk < 0) break;
         c = best_d;
         err = best;
+        if (target > 0) aoa = aoa_error(s, tx, rx, order, faces, c, txk);
         R *= shrink;
         if (choice) choice[it] = bk;
         ++it;
@@ -1383,10 +1405,45 @@ int64_t ora_diffract(void *sp, const double *tx3, const double *dirs, const int6
 }
 
 /*
+ * Diffraction point of the ray tx + s d (d unit): the point Q = a + u (b - a) of the edge
+ * line closest to the ray.  Writes u and the ray parameter s of the closest approach
+ * (both -1 for a ray parallel to the edge).
+ */
+static vec3 wedge_ray_point(const wedge_t *w, vec3 tx, vec3 d, double *u_out, double *s_out) {
+    /* closest points of the lines tx + s d and a + u (b - a) */
+    vec3 eb = sub(w->b, w->a), w0 = sub(tx, w->a);
+    double A = 1.0, B = dot(d, eb), C = dot(eb, eb), D = dot(d, w0), E = dot(eb, w0);
+    double den = A * C - B * B;
+    double u = den != 0.0 ? (A * E - B * D) / den : -1.0;
+    *u_out = u;
+    *s_out = den != 0.0 ? (B * E - C * D) / den : -1.0;
+    return add(w->a, scl(eb, u));
+}
+
+/*
+ * Exact diffraction point Q* of the pair (tx, rx) at wedge w: along the edge at z_T + (z_R
+ * - z_T) r_T / (r_T + r_R) (z: position along the edge, r: distance from it), where the
+ * segment Tx -> Rx* crosses the edge line.  Writes z; returns 0 if Tx lies on the line.
+ */
+static int wedge_exact_point(const wedge_t *w, vec3 tx, vec3 rx, vec3 *q_out, double *z_out) {
+    vec3 qt = sub(tx, w->a), qr = sub(rx, w->a);
+    double zt = dot(qt, w->e), zr = dot(qr, w->e);
+    double rt = norm(perp_to(qt, w->e)), rr = norm(perp_to(qr, w->e));
+    if (!(rt > 0.0)) return 0;
+    double z = zt + (zr - zt) * rt / (rt + rr);
+    *z_out = z;
+    *q_out = add(w->a, scl(w->e, z));
+    return 1;
+}
+
+/*
  * The precise algorithm (§III.B, Fig. 5, Eq. 10) for a diffraction path at wedge wi: the
  * same sub-ray pattern, argmin and shrink as ora_refine, with Eq. 3 evaluated in the
  * unfolded space of the wedge (see wedge_unfold_rx): error(d) = angle(d, Rx* - Tx) for
- * d . (Rx* - Tx) > 0, else +inf.  Returns iterations done (-1 for a bad K or Tx on the
+ * d . (Rx* - Tx) > 0, else +inf.  The early stop needs, as for reflections, both that
+ * error (the AOD error) and the AOA error <= target: the angle at Rx between the
+ * directions to the diffraction point of the current ray (wedge_ray_point) and to the
+ * exact one (wedge_exact_point).  Returns iterations done (-1 for a bad K or Tx on the
  * edge line).
  */
 int ora_refine_wedge(void *sp, const double *tx3, const double *rx3, int32_t wi, const double *c0, double R0,
@@ -1398,13 +1455,16 @@ int ora_refine_wedge(void *sp, const double *tx3, const double *rx3, int32_t wi,
     if (ora_subray_pattern(K, rho, phi, &shrink) != K) return -1;
     vec3 tx = ld(tx3), rx = ld(rx3), c = unit(ld(c0)), Rs;
     if (!wedge_unfold_rx(&s->wd[wi], tx, rx, &Rs)) return -1;
-    vec3 W = sub(Rs, tx);
+    vec3 W = sub(Rs, tx), Qs;
+    double zs, uq, sq;
+    wedge_exact_point(&s->wd[wi], tx, rx, &Qs, &zs);
     double R = R0;
     double err = dot(c, W) > 0.0 ? angle_between(c, W) : INFINITY;
+    double aoa = angle_between(sub(wedge_ray_point(&s->wd[wi], tx, unit(c), &uq, &sq), rx), sub(Qs, rx));
     if (err_hist) err_hist[0] = err;
     int it = 0;
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;   /* stalled paths stop, see ora_refine */
-    while (it < iters && !(target > 0 && err <= target) && !(err > R * stall + 1e-6)) {
+    while (it < iters && !(target > 0 && err <= target && aoa <= target) && !(err > R * stall + 1e-6)) {
         vec3 u, v, best_d = c;
         double best = INFINITY;
         int bk = -1;
@@ -1418,6 +1478,7 @@ int ora_refine_wedge(void *sp, const double *tx3, const double *rx3, int32_t wi,
         if (bk < 0) break;
         c = best_d;
         err = best;
+        aoa = angle_between(sub(wedge_ray_point(&s->wd[wi], tx, unit(c), &uq, &sq), rx), sub(Qs, rx));
         R *= shrink;
         if (choice) choice[it] = bk;
         ++it;
@@ -1451,13 +1512,8 @@ int ora_wedge_eval(void *sp, const double *tx3, const double *rx3, int32_t wi, c
     vec3 W = sub(Rs, tx);
     double e = dot(d, W) > 0.0 ? angle_between(d, W) : INFINITY;
     *err = e;
-    /* closest points of the lines tx + s d and a + u (b - a) */
-    vec3 eb = sub(w->b, w->a), w0 = sub(tx, w->a);
-    double A = 1.0, B = dot(d, eb), C = dot(eb, eb), D = dot(d, w0), E = dot(eb, w0);
-    double den = A * C - B * B;
-    double u = den != 0.0 ? (A * E - B * D) / den : -1.0;
-    double sq = den != 0.0 ? (B * E - C * D) / den : -1.0;
-    vec3 Q = add(w->a, scl(eb, u));
+    double u, sq;
+    vec3 Q = wedge_ray_point(w, tx, d, &u, &sq);
     if (q_out) st(q_out, Q);
     int ok = u >= 0.0 && u <= 1.0 && sq > 0.0 && wedge_exterior(w, tx) && wedge_exterior(w, rx);
     if (ok && (occluded(s, tx, Q, w->f1, w->f2) || occluded(s, Q, rx, w->f1, w->f2))) ok = 0;
@@ -1483,13 +1539,9 @@ int ora_wedge_image(void *sp, const double *tx3, const double *rx3, int32_t wi, 
     scene *s = (scene *)sp;
     wedges_build(s);
     const wedge_t *w = &s->wd[wi];
-    vec3 tx = ld(tx3), rx = ld(rx3);
-    vec3 qt = sub(tx, w->a), qr = sub(rx, w->a);
-    double zt = dot(qt, w->e), zr = dot(qr, w->e);
-    double rt = norm(perp_to(qt, w->e)), rr = norm(perp_to(qr, w->e));
-    if (!(rt > 0.0)) return -1;
-    double z = zt + (zr - zt) * rt / (rt + rr);
-    vec3 Q = add(w->a, scl(w->e, z));
+    vec3 tx = ld(tx3), rx = ld(rx3), Q;
+    double z;
+    if (!wedge_exact_point(w, tx, rx, &Q, &z)) return -1;
     st(q_out, Q);
     vec3 dir = unit(sub(Q, tx));
     st(aod_dir, dir);

@@ -617,6 +617,7 @@ sbr_status sbr_paths_create(sbr_ctx *ctx, int64_t record_cap, int64_t path_cap, 
     cv.add(&p->unf, (size_t)path_cap * kUnfStride);
     cv.add(&p->order_idx, (size_t)path_cap);
     cv.add(&p->order_cnt, (size_t)32);
+    cv.add(&p->fp64_idx, (size_t)path_cap);
     cv.add(&table, (size_t)slots * 2 + (size_t)(slots + 1) / 2);   // keys, values, winner ids
     cv.add(&p->counters, (size_t)kNumCounters);
     p->mem = dev_alloc(ctx, cv.total);
@@ -815,6 +816,7 @@ static sbr_status refine_args(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *p
     A.unf = paths->unf;
     A.order_idx = paths->order_idx;
     A.order_cnt = paths->order_cnt;
+    A.fp64_idx = paths->fp64_idx;
     A.counters = paths->counters;
     A.path_cap = paths->path_cap;
     A.range = nullptr;

@@ -224,10 +224,54 @@ __device__ __forceinline__ double key64(const UnfD &u, int k, dvec3 d, double &d
     return ddot(c, c);
 }
 
-// The iteration stops early once the error angle is <= target: for an angle below pi/2,
-// atan2(sqrt(key), dw) <= target  <=>  key <= dw^2 tan^2(target).
-__device__ __forceinline__ bool reached(const RefineArgs &A, double key, double dw) {
-    return A.target > 0.0 && key < INFINITY && key <= dw * dw * A.tan2_target;
+// The iteration stops early once the path meets the accuracy requirement (§III.B): its AOD
+// error, which is Eq. 3's error angle, and its AOA error both <= target.  For an angle
+// below pi/2, atan2(sqrt(key), dw) <= target  <=>  key <= dw^2 tan^2(target).
+// The AOA is the direction from Rx to the path's last bounce point (a diffraction path's
+// edge point Q).  Unfolding is an isometry, so the AOA error is the angle at Rx' between
+// X - W and -W, with X the unfolded last point relative to Tx (T_k d for reflections, Q -
+// Tx for diffraction: the rotation about the edge fixes Q): the exact last point lies on
+// the segment Tx -> Rx'.  tan(AOA error) = |X x W| / (W . W - X . W).  LOS paths have no
+// AOA error (their AOA points at Tx for every launch direction).  d is a unit vector.
+// Operands by value: P = the unfolded last plane (n'_k, num_k) of a reflection path, W =
+// Rx' - Tx, wp = the wedge record of a diffraction path (else null).
+__device__ __forceinline__ bool aoa_within64(dvec3 d, D4 P, D4 Wv, const float4 *wp, dvec3 tx, double tan2) {
+    dvec3 X;
+    if (wp) {
+        const float4 A0 = __ldg(wp), B0 = __ldg(wp + 1);
+        const dvec3 a = dv(A0.x, A0.y, A0.z), eb = dv(B0.x, B0.y, B0.z) - a, w0 = tx - a;
+        const double b = ddot(d, eb), den = ddot(eb, eb) - b * b;
+        if (!(den > 0.0)) return false;
+        X = eb * ((ddot(eb, w0) - b * ddot(d, w0)) / den) - w0;
+    } else {
+        X = d * (P.w / ddot(dv(P.x, P.y, P.z), d));
+    }
+    const dvec3 W = dv(Wv.x, Wv.y, Wv.z), c = dcross(X, W);
+    const double h = ddot(W, W) - ddot(X, W);
+    return h > 0.0 && ddot(c, c) <= h * h * tan2;
+}
+
+__device__ __forceinline__ bool aoa_within32(float3 d, float4 P, float4 Wv, const float4 *wp, float3 tx, float tan2) {
+    float3 X;
+    if (wp) {
+        const float3 a = f3(__ldg(wp)), eb = f3(__ldg(wp + 1)) - a, w0 = tx - a;
+        const float b = dot(d, eb), den = dot(eb, eb) - b * b;
+        if (!(den > 0.0f)) return false;
+        X = eb * ((dot(eb, w0) - b * dot(d, w0)) / den) - w0;
+    } else {
+        X = d * (P.w / dot(make_float3(P.x, P.y, P.z), d));
+    }
+    const float3 W = make_float3(Wv.x, Wv.y, Wv.z), c = cross(X, W);
+    const float h = dot(W, W) - dot(X, W);
+    return h > 0.0f && dot(c, c) <= h * h * tan2;
+}
+
+__device__ __forceinline__ bool reached(const RefineArgs &A, const PathGeo &g, const UnfD &ud, dvec3 c, double key,
+                                        double dw) {
+    if (!(A.target > 0.0 && key < INFINITY && key <= dw * dw * A.tan2_target)) return false;
+    if (g.wedge < 0 && g.k == 0) return true;
+    const float4 *wp = g.wedge >= 0 ? A.scene.wedges + 4 * (size_t)g.wedge : nullptr;
+    return aoa_within64(c, wp ? ud.w : ud.p[g.k - 1], ud.w, wp, g.txd, A.tan2_target);
 }
 
 // A stalled path stops: once its error angle exceeds R (1 / (1 - s) + 2 s) + 1e-6 it can
@@ -240,8 +284,12 @@ __device__ __forceinline__ bool stalled(double key, double dw, double R, double 
     return atan2f(sqrtf((float)key), (float)dw) > (float)(R * stall + 1e-6);
 }
 
-__device__ __forceinline__ bool reached32(const RefineArgs &A, float key, float dw) {
-    return A.target_on && key < INFINITY && key <= dw * dw * A.tan2_target_f;
+__device__ __forceinline__ bool reached32(const RefineArgs &A, const PathGeo &g, const UnfF &uf, float3 c, float key,
+                                          float dw) {
+    if (!(A.target_on && key < INFINITY && key <= dw * dw * A.tan2_target_f)) return false;
+    if (g.wedge < 0 && g.k == 0) return true;
+    const float4 *wp = g.wedge >= 0 ? A.scene.wedges + 4 * (size_t)g.wedge : nullptr;
+    return aoa_within32(c, wp ? uf.w : uf.p[g.k - 1], uf.w, wp, g.tx, A.tan2_target_f);
 }
 
 __device__ __forceinline__ bool stalled32(float key, float dw, float Rf, float stall) {
@@ -639,7 +687,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
         int it = 0, flags = 0;
         if (!fp64) {
             keyf = key32(uf, g.k, cf, dwf);
-            while (it < A.max_iters && !reached32(A, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
+            while (it < A.max_iters && !reached32(A, g, uf, cf, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
                    !(Rf < A.fp64_below_f)) {
                 const int bk = iterate32(uf, g.k, A.K, off, Rf, cf, keyf, dwf);
                 if (bk < 0) {
@@ -662,7 +710,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
                 key = keyf;
                 dw = dwf;
             }
-            while (it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
+            while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
                 const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
                 if (bk < 0) {
                     fail = true;
@@ -676,7 +724,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
             }
         }
         if (fail) flags |= SBR_PATH_TRACE_FAIL;
-        else if (it < A.max_iters && !(fp64 ? reached(A, key, dw) : reached32(A, keyf, dwf)))
+        else if (it < A.max_iters && !(fp64 ? reached(A, g, ud, c, key, dw) : reached32(A, g, uf, cf, keyf, dwf)))
             flags |= SBR_PATH_STALLED;
         p.iters = it;
         p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
@@ -848,8 +896,10 @@ __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
     }
 }
 
+// At most 85 registers a thread, so that three 256-thread blocks fit on an SM (measured
+// faster than the uncapped 124-128 registers of the 8- and 32-lane forms).
 template <int G>
-__global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
+__global__ void __launch_bounds__(256, 3) batch_refine_kernel(RefineArgs A) {
     // the unfolded planes of each group's current path (shared by its G lanes)
     __shared__ UnfD s_ud[256 / G];
     __shared__ UnfF s_uf[256 / G];
@@ -904,7 +954,7 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
         int it = 0, flags = 0;
         if (!fp64) {
             keyf = key32(uf, g.k, cf, dwf);
-            while (it < A.max_iters && !reached32(A, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
+            while (it < A.max_iters && !reached32(A, g, uf, cf, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
                    !(Rf < A.fp64_below_f)) {
                 const int bk = group_iterate32<G>(uf, g.k, A.K, off, Rf, cf, keyf, dwf, gl, gmask);
                 if (bk < 0) {
@@ -918,13 +968,22 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
         }
         dvec3 c;
         double key = INFINITY, dw = 0.0;
-        if (!fail && Rf < A.fp64_below_f) {
-            // the FP64 phase needs the FP64 planes: built here if only the FP32 copy was read
-            if (prebuilt) {
-                if (gl < g.k) ud.p[gl] = unfold_plane(A.scene, g, gl);
-                if (gl == G - 1) ud.w = unfold_rx(A.scene, g);
-                __syncwarp(gmask);
+        if (!fail && Rf < A.fp64_below_f && prebuilt) {
+            // many paths: the FP64 iterations run in batch_refine64_kernel, one thread per
+            // path.  The record keeps the iterations done; the path's unf slot keeps the
+            // cone centre and |d x W|^2 of the FP32 phase, the record's err field d . W.
+            if (gl == 0) {
+                sbr_path_record *dst = A.paths + pi;
+                dst->iters = it;
+                dst->err = dwf;
+                A.unf[kUnfStride * pi + kMaxOrder + 1] = make_float4(cf.x, cf.y, cf.z, keyf);
+                const unsigned long long at =
+                    atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kFp64Count), 1ULL);
+                A.fp64_idx[at] = (int)pi;
             }
+            continue;
+        }
+        if (!fail && Rf < A.fp64_below_f) {
             double R = cone_radius64(A, p.rough_err, it, shrink);
             if (fp64) {
                 c = dv(p.dir[0], p.dir[1], p.dir[2]);
@@ -934,7 +993,7 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
                 key = keyf;
                 dw = dwf;
             }
-            while (it < A.max_iters && !reached(A, key, dw) && !stalled(key, dw, R, stall)) {
+            while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
                 const int bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
                 if (bk < 0) {
                     fail = true;
@@ -948,7 +1007,7 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
             }
         }
         if (fail) flags |= SBR_PATH_TRACE_FAIL;
-        else if (it < A.max_iters && !(fp64 ? reached(A, key, dw) : reached32(A, keyf, dwf)))
+        else if (it < A.max_iters && !(fp64 ? reached(A, g, ud, c, key, dw) : reached32(A, g, uf, cf, keyf, dwf)))
             flags |= SBR_PATH_STALLED;
         if (gl == 0) {
             if (!fp64) c = dv(cf.x, cf.y, cf.z);
@@ -976,6 +1035,81 @@ __global__ void __launch_bounds__(256) batch_refine_kernel(RefineArgs A) {
             dst->err = p.err;
             dst->flags = p.flags;
         }
+    }
+}
+
+// Batched form, FP64 tail (from split_min paths on), one thread per path: the paths whose
+// cone fell below fp64_below in batch_refine_kernel continue here with the plain form's
+// FP64 iterations (iterate64, all K sub-rays in one thread), so that each instruction of
+// GB300's narrow FP64 pipe serves 32 paths, where a lane group serves one.  The state
+// carried over, and the arithmetic, are those of the in-group FP64 phase: a path that
+// started in FP64 (no iteration done) takes its FP64 rough direction; otherwise the FP32
+// phase's centre with its |d x W|^2 and d . W.  The path is then listed in its order group
+// for batch_finalize_kernel.
+__global__ void __launch_bounds__(128) batch_refine64_kernel(RefineArgs A) {
+    const long long n = A.counters[kFp64Count];
+    const int off = c_sub.off[A.K];
+    const double shrink = c_sub.shrink[A.K];
+    const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long pi = A.fp64_idx[t];
+        sbr_path_record p = A.paths[pi];
+        PathGeo g;
+        load_path(A, p, g);
+        UnfD ud;
+        UnfF uf;
+        const float4 *u = A.unf + kUnfStride * pi;
+        for (int j = 0; j < g.k; ++j) {
+            ud.p[j] = unfold_plane(A.scene, g, j);
+            uf.p[j] = u[j];
+        }
+        ud.w = unfold_rx(A.scene, g);
+        uf.w = u[kMaxOrder];
+        const float4 cu = u[kMaxOrder + 1];
+        const float3 cf = f3(cu);
+        const float keyf = cu.w, dwf = (float)p.err;
+        int it = p.iters, flags = 0;
+        bool fp64 = it == 0, fail = false;
+        double R = cone_radius64(A, p.rough_err, it, shrink);
+        dvec3 c;
+        double key, dw = 0.0;
+        if (fp64) {
+            c = dv(p.dir[0], p.dir[1], p.dir[2]);
+            key = key64(ud, g.k, c, dw);
+        } else {
+            c = dv(cf.x, cf.y, cf.z);
+            key = keyf;
+            dw = dwf;
+        }
+        while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
+            const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
+            if (bk < 0) {
+                fail = true;
+                break;
+            }
+            flags |= SBR_PATH_FP64;
+            fp64 = true;
+            if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+            R *= shrink;
+            ++it;
+        }
+        if (fail) flags |= SBR_PATH_TRACE_FAIL;
+        else if (it < A.max_iters && !(fp64 ? reached(A, g, ud, c, key, dw) : reached32(A, g, uf, cf, keyf, dwf)))
+            flags |= SBR_PATH_STALLED;
+        if (!fp64) c = dv(cf.x, cf.y, cf.z);
+        const int grp = order_group(g);
+        unsigned long long at = 0;
+        for (int b = 0; b < grp; ++b) at += A.order_cnt[b];
+        at += atomicAdd(A.order_cnt + 16 + grp, 1ULL);
+        A.order_idx[at] = (int)pi;
+        sbr_path_record *dst = A.paths + pi;
+        dst->iters = it;
+        dst->dir[0] = c.x;
+        dst->dir[1] = c.y;
+        dst->dir[2] = c.z;
+        dst->err = error_angle(key, dw, keyf, dwf, fp64);
+        dst->flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
     }
 }
 
@@ -1090,6 +1224,8 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
     }
     e = cudaMemsetAsync(a.order_cnt, 0, 32 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(a.counters + kFp64Count, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return e;
     batch_unfold_kernel<<<sms * unf_blocks, 128, 0, s>>>(a);
     switch (a.chunk) {
         case 8: batch_refine_kernel<8><<<grid, block, 0, s>>>(a); break;
@@ -1098,6 +1234,12 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    static int tail_blocks = 0;
+    if (!tail_blocks) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tail_blocks, batch_refine64_kernel, 128, 0);
+        if (tail_blocks < 1) tail_blocks = 1;
+    }
+    batch_refine64_kernel<<<sms * tail_blocks, 128, 0, s>>>(a);
     static int fin_blocks = 0;
     if (!fin_blocks) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fin_blocks, batch_finalize_kernel, 128, 0);

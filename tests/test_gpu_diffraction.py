@@ -121,6 +121,50 @@ def test_refined_diffraction_vs_oracle_and_exact(gpu_ctx, oracle_mod, block):
     assert valid == exact and checked > 5
 
 
+def test_early_stop_diffraction(gpu_ctx, oracle_mod, block):
+    """Early stop at 0.01 deg (§III.B: the iteration ends once the path is accurate
+    enough) for order-1 diffraction paths (and the block's few reflections): the plain and
+    batched forms agree, the iteration counts match the oracle's (argmin near-ties aside),
+    and every path that stopped before the cap has its AOD and AOA within the target of the
+    exact path (exact diffraction point / image method)."""
+    sc, tx, rx, n, S, scene, rxs, paths, ora, dr = block
+    cap, target = 12, np.radians(0.01)
+    res = []
+    for mode in ("plain", "batch"):
+        gpu_ctx.launch(scene, tx, rxs, paths, n, 2, rx_angle_scale=SQ3, sync=True, diffraction=True)
+        if mode == "plain":
+            gpu_ctx.refine(scene, paths, cap, 9, target=target)
+        else:
+            gpu_ctx.batch_refine(scene, paths, cap, 9, target=target)
+        got = gpu_ctx.query(paths)
+        res.append({(int(g["tx"]), int(g["rx"]), int(g["order"]), tuple(int(f) for f in g["faces"][: g["order"]])): g
+                    for g in got})
+    assert set(res[0]) == set(res[1])
+    for k, g in res[0].items():
+        assert g["iters"] == res[1][k]["iters"] and ang(g["dir"], res[1][k]["dir"]) < 1e-9
+    tl = oracle_mod.theta_launch(n)
+    near = early = early_diff = 0
+    for (t, r, k, faces), g in res[1].items():
+        c0 = oracle_mod.lattice_ids(n, [int(g["ray"])])[0]
+        R0 = max(tl, float(g["rough_err"]))
+        diff = k == 1 and faces[0] < 0
+        if diff:
+            w = -1 - faces[0]
+            ref = oracle_mod.refine_wedge(S, tx[t], rx[r], w, c0, R0, 9, cap, target)
+        else:
+            ref = oracle_mod.refine(S, tx[t], rx[r], faces, c0, R0, 9, cap, target)
+        if int(g["iters"]) != ref["iters"]:
+            near += 1
+        if not g["valid"] or int(g["iters"]) >= cap:
+            continue
+        ex = oracle_mod.wedge_image(S, tx[t], rx[r], w) if diff else oracle_mod.image_path(S, tx[t], rx[r], faces)
+        assert ang(g["dir"], ex["aod_dir"]) <= target * (1 + 1e-3) + 1e-6
+        assert ang(dir_of(*g["aoa"]), dir_of(*ex["aoa"])) <= target * (1 + 1e-3) + 1e-6
+        early += 1
+        early_diff += diff
+    assert near <= 0.1 * len(res[1]) and early_diff > 10
+
+
 def test_diffraction_leaves_reflections_alone(gpu_ctx, block):
     """The diffraction search only adds paths: the reflection paths of a launch with it
     equal those of a launch without it."""

@@ -79,13 +79,33 @@ def test_refinement_k6_sixty_iterations_plateau(oracle_mod, shoebox_run):
 
 
 def test_early_stop_at_target(oracle_mod, shoebox_run):
+    """§III.B: the iteration stops once the path meets the accuracy requirement, its AOD
+    and AOA both within the target.  Checked against the image method: at the stop both
+    errors are <= target, one iteration earlier at least one was not.  The AOA part
+    matters: some paths meet the AOD target iterations before their AOA does."""
     S, tx, rx, res, im = shoebox_run
     tl = oracle_mod.theta_launch(64)
     target = np.radians(0.01)
-    for p in res.paths[:20]:
-        r = oracle_mod.refine(S, tx[0], rx[0], p["faces"], p["rough_dir"], max(tl, p["err"]), 9, 8, target)
-        assert r["err"] <= target
-        assert r["iters"] == 0 or r["err_hist"][-2] > target
+
+    def errors(p, d):
+        ev = oracle_mod.path_eval(S, tx[0], rx[0], p["faces"], d)
+        q = oracle_mod.image_path(S, tx[0], rx[0], p["faces"])
+        return _ang(d, q["aod_dir"]), _ang(_dir(*ev["aoa"]), _dir(*q["aoa"]))
+
+    aod_first = 0
+    for p in res.paths:
+        R0 = max(tl, p["err"])
+        r = oracle_mod.refine(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 9, 12, target)
+        assert r["iters"] < 12
+        aod, aoa = errors(p, r["dir"])
+        assert abs(aod - r["err"]) < 1e-12 and aod <= target and aoa <= target * (1 + 1e-9)
+        if r["iters"] > 0:
+            q = oracle_mod.refine(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 9, r["iters"] - 1, target)
+            assert np.array_equal(q["choice"], r["choice"][:-1])
+            aod1, aoa1 = errors(p, q["dir"])
+            assert aod1 > target or aoa1 > target
+            aod_first += aod1 <= target
+    assert aod_first >= 5
 
 
 def test_pipeline_matches_image_method(oracle_mod, shoebox_run):
