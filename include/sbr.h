@@ -239,12 +239,13 @@ sbr_status sbr_refine_pair(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *path
 typedef struct {
     int32_t block_threads;   /* threads per block (0 = 128) */
     int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid (0 = max) */
-    int32_t lanes_per_path;  /* lanes cooperating on one path: 8, 16 or 32 (0 = 16) */
+    int32_t lanes_per_path;  /* lanes cooperating on one path: 1, 8, 16 or 32 (0 = 16) */
 } sbr_batch_config;
 
 /* a9 -- batched form of a6-a8: one persistent launch refines all paths of all (Tx, Rx)
  * pairs.  A group of lanes_per_path lanes owns one path: its lanes evaluate the K
- * sub-rays of an iteration in parallel; a group that finishes a path (iteration cap,
+ * sub-rays of an iteration in parallel (one lane: all K in turn, the form for many
+ * paths); a group that finishes a path (iteration cap,
  * target reached, stalled) takes the next one from a device work queue (atomic head), so
  * uneven iteration counts do not idle the GPU.  A second launch runs the validity test and
  * outputs (one thread per path when there are many, one warp per path when there are

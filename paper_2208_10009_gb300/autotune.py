@@ -1,7 +1,7 @@
 """Autotuner for the batched refinement kernel's launch shape.
 
 The batched kernel's speed depends on the block size, on how many lanes cooperate on one
-path (8, 16 or 32) and on how many blocks stay resident per SM; the best choice depends on
+path (1, 8, 16 or 32) and on how many blocks stay resident per SM; the best choice depends on
 the number of paths, their orders and iteration counts.  `tune_batch_refine` times every
 combination on the caller's own paths (refinement rewrites the paths in place, so the
 caller supplies `relaunch`, which must regenerate the rough paths before each trial) and
@@ -43,7 +43,7 @@ def _save_file():
 
 
 def tune_batch_refine(ctx, scene, paths, relaunch, max_iters: int, K: int, target: float = 0.0, trials: int = 3,
-                      blocks=(64, 128, 256), lanes=(8, 16, 32), per_sm=(0, 4, 2), force: bool = False) -> dict:
+                      blocks=(64, 128, 256), lanes=(1, 8, 16, 32), per_sm=(0, 4, 2), force: bool = False) -> dict:
     """Return {"block_threads", "lanes_per_path", "blocks_per_sm", "ms", "table"} for the
     fastest batched-refinement launch shape on these paths."""
     _load_file()

@@ -906,12 +906,13 @@ sbr_status sbr_batch_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *pat
     if (block % 32 != 0 || block > 256)
         return fail(ctx, SBR_EINVAL, "sbr_batch_refine: block_threads must be a multiple of 32, at most 256");
     int lanes = cfg && cfg->lanes_per_path > 0 ? cfg->lanes_per_path : 16;
-    if (lanes != 8 && lanes != 16 && lanes != 32)
-        return fail(ctx, SBR_EINVAL, "sbr_batch_refine: lanes_per_path must be 8, 16 or 32");
+    if (lanes != 1 && lanes != 8 && lanes != 16 && lanes != 32)
+        return fail(ctx, SBR_EINVAL, "sbr_batch_refine: lanes_per_path must be 1, 8, 16 or 32");
     int nb = 1;
     refine_kernel_attrs(nullptr, block, &nb, true, lanes);
     if (cfg && cfg->blocks_per_sm > 0) nb = std::min(nb, cfg->blocks_per_sm);
     A.chunk = lanes;
+    if (lanes == 1) A.split_min = 0;   // the one-lane form runs with the unfold and FP64 tail kernels
     SBR_CUDA(launch_batch_refine(A, ctx->num_sms * nb, block, ctx->stream));
     return SBR_OK;
 }

@@ -898,15 +898,19 @@ __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
 
 // At most 85 registers a thread, so that three 256-thread blocks fit on an SM (measured
 // faster than the uncapped 124-128 registers of the 8- and 32-lane forms).
+// G = 1 is the one-lane form: each thread evaluates all K sub-rays of its own path (no
+// shuffles, no re-evaluation of the winner) and always runs with batch_unfold_kernel and
+// the FP64 tail kernel (the host sets split_min = 0 for it).
 template <int G>
-__global__ void __launch_bounds__(256, 3) batch_refine_kernel(RefineArgs A) {
+__global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(RefineArgs A) {
     // the unfolded planes of each group's current path (shared by its G lanes)
-    __shared__ UnfD s_ud[256 / G];
+    __shared__ UnfD s_ud[G == 1 ? 1 : 256 / G];
     __shared__ UnfF s_uf[256 / G];
-    UnfD &ud = s_ud[threadIdx.x / G];
+    UnfD &ud = s_ud[G == 1 ? 0 : threadIdx.x / G];   // unused by the one-lane form
     UnfF &uf = s_uf[threadIdx.x / G];
     const long long total = path_count(A);
-    const bool prebuilt = total >= A.split_min;   // batch_unfold_kernel ran
+    // batch_unfold_kernel ran (the one-lane form always runs with it: split_min = 0)
+    const bool prebuilt = G == 1 || total >= A.split_min;
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
     const float shrinkf = c_sub.shrink_f[A.K];
@@ -917,8 +921,18 @@ __global__ void __launch_bounds__(256, 3) batch_refine_kernel(RefineArgs A) {
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - gl));
     for (;;) {
         unsigned long long q = 0;
-        if (gl == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kBatchHead), 1ULL);
-        q = __shfl_sync(gmask, q, 0, G);
+        if (G == 1) {
+            // the lanes that finished a path together take consecutive indices with one atomic
+            const unsigned m = __activemask();
+            const int leader = __ffs(m) - 1;
+            if (lane == leader)
+                q = atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kBatchHead),
+                              (unsigned long long)__popc(m));
+            q = __shfl_sync(m, q, leader) + __popc(m & ((1u << lane) - 1u));
+        } else {
+            if (gl == 0) q = atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kBatchHead), 1ULL);
+            q = __shfl_sync(gmask, q, 0, G);
+        }
         if ((long long)q >= total) break;
         const long long pi = (long long)q;
         sbr_path_record p = A.paths[pi];
@@ -942,7 +956,7 @@ __global__ void __launch_bounds__(256, 3) batch_refine_kernel(RefineArgs A) {
                 if (j < g.k || j == kMaxOrder) (j < kMaxOrder ? uf.p[j] : uf.w) = A.unf[kUnfStride * pi + j];
             cf = f3(A.unf[kUnfStride * pi + kMaxOrder + 1]);
         } else {
-            if (gl < g.k) set_unf(ud, uf, gl, unfold_plane(A.scene, g, gl));
+            for (int j = gl; j < g.k; j += G) set_unf(ud, uf, j, unfold_plane(A.scene, g, j));
             if (gl == G - 1) set_unf(ud, uf, kMaxOrder, unfold_rx(A.scene, g));
             cf = make_float3((float)p.dir[0], (float)p.dir[1], (float)p.dir[2]);
         }
@@ -956,7 +970,8 @@ __global__ void __launch_bounds__(256, 3) batch_refine_kernel(RefineArgs A) {
             keyf = key32(uf, g.k, cf, dwf);
             while (it < A.max_iters && !reached32(A, g, uf, cf, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
                    !(Rf < A.fp64_below_f)) {
-                const int bk = group_iterate32<G>(uf, g.k, A.K, off, Rf, cf, keyf, dwf, gl, gmask);
+                const int bk = G == 1 ? iterate32(uf, g.k, A.K, off, Rf, cf, keyf, dwf)
+                                      : group_iterate32<G>(uf, g.k, A.K, off, Rf, cf, keyf, dwf, gl, gmask);
                 if (bk < 0) {
                     fail = true;
                     break;
@@ -983,7 +998,7 @@ __global__ void __launch_bounds__(256, 3) batch_refine_kernel(RefineArgs A) {
             }
             continue;
         }
-        if (!fail && Rf < A.fp64_below_f) {
+        if (G != 1 && !fail && Rf < A.fp64_below_f) {
             double R = cone_radius64(A, p.rough_err, it, shrink);
             if (fp64) {
                 c = dv(p.dir[0], p.dir[1], p.dir[2]);
@@ -1188,6 +1203,7 @@ __global__ void __launch_bounds__(128, 8) batch_finalize_kernel(RefineArgs A) {
 
 static const void *batch_fn(int lanes) {
     switch (lanes) {
+        case 1: return (const void *)batch_refine_kernel<1>;
         case 8: return (const void *)batch_refine_kernel<8>;
         case 32: return (const void *)batch_refine_kernel<32>;
         default: return (const void *)batch_refine_kernel<16>;
@@ -1228,6 +1244,7 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
     if (e != cudaSuccess) return e;
     batch_unfold_kernel<<<sms * unf_blocks, 128, 0, s>>>(a);
     switch (a.chunk) {
+        case 1: batch_refine_kernel<1><<<grid, block, 0, s>>>(a); break;
         case 8: batch_refine_kernel<8><<<grid, block, 0, s>>>(a); break;
         case 32: batch_refine_kernel<32><<<grid, block, 0, s>>>(a); break;
         default: batch_refine_kernel<16><<<grid, block, 0, s>>>(a); break;

@@ -218,7 +218,7 @@ def test_batched_and_per_pair_equal_plain(gpu_ctx, oracle_mod):
     sc, tx, rx = scenes.office(nbox=60, ntx=2, nrx=12, g_shell=8, g_box=1)
     scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx, 1 << 18, 1 << 16)
     res = []
-    for mode in ("plain", "batch", "batch8", "batch32", "pair"):
+    for mode in ("plain", "batch", "batch8", "batch32", "batch1", "pair"):
         gpu_ctx.launch(scene, tx, rxs, paths, 48, 3, rx_angle_scale=SQ3, sync=True)
         if mode == "plain":
             gpu_ctx.refine(scene, paths, 8, 16, target=np.radians(0.01))
