@@ -244,7 +244,11 @@ def run_gpu(args):
     def relaunch():
         ctx.launch(scene, tx_dev, rxs, paths, n, order, rx_angle_scale=alpha, **LAUNCH_OPTS)
 
-    tuned = autotune.tune_batch_refine(ctx, scene, paths, relaunch, iters, K, target=target)
+    if args.batch_shape:
+        b, l, sm = (int(x) for x in args.batch_shape.split(","))
+        tuned = {"block_threads": b, "lanes_per_path": l, "blocks_per_sm": sm, "ms": None}
+    else:
+        tuned = autotune.tune_batch_refine(ctx, scene, paths, relaunch, iters, K, target=target)
     shape = {k: tuned[k] for k in ("block_threads", "lanes_per_path", "blocks_per_sm")}
 
     def step():
@@ -541,6 +545,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="canyon", choices=sorted(WORKLOADS) + ["grad"])
+    ap.add_argument("--batch-shape", default="",
+                    help="block_threads,lanes_per_path,blocks_per_sm of the batched refinement (default: autotuned)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3

@@ -987,13 +987,17 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
             // many paths: the FP64 iterations run in batch_refine64_kernel, one thread per
             // path.  The record keeps the iterations done; the path's unf slot keeps the
             // cone centre and |d x W|^2 of the FP32 phase, the record's err field d . W.
+            // Listed by order group (group offsets from batch_unfold_kernel's counts), so that
+            // the tail kernel's warps run paths of one order.
             if (gl == 0) {
                 sbr_path_record *dst = A.paths + pi;
                 dst->iters = it;
                 dst->err = dwf;
                 A.unf[kUnfStride * pi + kMaxOrder + 1] = make_float4(cf.x, cf.y, cf.z, keyf);
-                const unsigned long long at =
-                    atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kFp64Count), 1ULL);
+                const int grp = order_group(g);
+                unsigned long long at = 0;
+                for (int b = 0; b < grp; ++b) at += A.order_cnt[b];
+                at += atomicAdd(A.order_cnt + 32 + grp, 1ULL);
                 A.fp64_idx[at] = (int)pi;
             }
             continue;
@@ -1062,13 +1066,22 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
 // phase's centre with its |d x W|^2 and d . W.  The path is then listed in its order group
 // for batch_finalize_kernel.
 __global__ void __launch_bounds__(128) batch_refine64_kernel(RefineArgs A) {
-    const long long n = A.counters[kFp64Count];
+    // the list holds group b's n_b paths from the group's offset (the sizes of groups < b)
+    long long n = 0;
+    for (int b = 0; b < 10; ++b) n += A.order_cnt[32 + b];
     const int off = c_sub.off[A.K];
     const double shrink = c_sub.shrink[A.K];
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x) {
-        const long long pi = A.fp64_idx[t];
+        long long slot = t, base = 0;
+        for (int b = 0; b < 10; ++b) {
+            const long long nb = (long long)A.order_cnt[32 + b];
+            if (slot < nb) break;
+            slot -= nb;
+            base += (long long)A.order_cnt[b];
+        }
+        const long long pi = A.fp64_idx[base + slot];
         sbr_path_record p = A.paths[pi];
         PathGeo g;
         load_path(A, p, g);
@@ -1238,9 +1251,7 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&unf_blocks, batch_unfold_kernel, 128, 0);
         if (unf_blocks < 1) unf_blocks = 1;
     }
-    e = cudaMemsetAsync(a.order_cnt, 0, 32 * sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(a.counters + kFp64Count, 0, sizeof(long long), s);
+    e = cudaMemsetAsync(a.order_cnt, 0, 48 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     batch_unfold_kernel<<<sms * unf_blocks, 128, 0, s>>>(a);
     switch (a.chunk) {
