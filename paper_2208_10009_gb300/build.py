@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 SO = os.path.join(OUT, "libsbr.so")
-SOURCES = ["capi.cu", "host_geometry.cpp", "host_wedges.cpp", "kernels_trace.cu", "kernels_diffract.cu",
+SOURCES = ["capi.cu", "host_geometry.cpp", "host_wedges.cpp", "host_faces.cpp", "kernels_trace.cu", "kernels_diffract.cu",
            "kernels_paths.cu", "kernels_refine.cu", "kernels_unfold.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -424,8 +424,13 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
         pl4[f] = make_float4((float)planes[f].x, (float)planes[f].y, (float)planes[f].z, (float)planes[f].w);
         if (face_eps) eps[f] = face_eps[f];
     }
+    std::vector<int2> outline;
+    std::vector<float4> corners;
+    build_face_outlines(verts, tris, tri_face, nt, nf, planes.data(), outline, corners);
     sbr_scene *sc = new (std::nothrow) sbr_scene();
     if (!sc) return fail(ctx, SBR_ENOMEM, "scene: host allocation failed");
+    int2 *d_ol;
+    float4 *d_olv;
     float4 *d_nodes, *d_nodes4, *d_tris, *d_pl;
     Plane64 *d_pld;
     float *d_eps;
@@ -443,6 +448,8 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     cv.add(&d_w, w4.size());
     cv.add(&d_wn, wbvh.nodes.size());
     cv.add(&d_wid, wids.size());
+    cv.add(&d_ol, outline.size());
+    cv.add(&d_olv, corners.size());
     sc->mem = dev_alloc(ctx, cv.total);
     if (!sc->mem) {
         delete sc;
@@ -462,6 +469,8 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     SBR_CUDA(cudaMemcpyAsync(d_w, w4.data(), w4.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_wn, wbvh.nodes.data(), wbvh.nodes.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_wid, wids.data(), wids.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    SBR_CUDA(cudaMemcpyAsync(d_ol, outline.data(), outline.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    SBR_CUDA(cudaMemcpyAsync(d_olv, corners.data(), corners.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaStreamSynchronize(s));
     sc->dev.nodes = d_nodes;
     sc->dev.nodes4 = d_nodes4;
@@ -471,6 +480,8 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     sc->dev.face_eps = d_eps;
     sc->dev.face_tri_off = d_off;
     sc->dev.face_tri_idx = d_idx;
+    sc->dev.face_outline = d_ol;
+    sc->dev.outline_v = d_olv;
     sc->dev.nt = (int)nt;
     sc->dev.nf = nf;
     sc->dev.nnodes = (int)(bvh.nodes.size() / 4);

@@ -421,7 +421,44 @@ __device__ __forceinline__ int iterate64(const UnfD &ud, int nk, int K, int off,
 }
 
 // ----------------------------------------------------------------------------- a7/a8
+// p lies in (or on the boundary of) face f's convex outline: every edge function
+// cross(b - a, p - a) . n of the counter-clockwise corners is >= 0.  FP32 with the
+// triangle test's rounding band below; a sign inside the band is decided in FP64.
+__device__ __noinline__ bool point_in_outline(const SceneDev &S, int f, int2 ol, dvec3 p) {
+    const float3 nf = f3(__ldg(S.planes + f));
+    const float3 P = make_float3((float)p.x, (float)p.y, (float)p.z);
+    const float pn = fabsf(P.x) + fabsf(P.y) + fabsf(P.z) + 1.0f;
+    const float4 *cv = S.outline_v + ol.x;
+    bool unsure = false;
+    float3 a = f3(__ldg(cv + ol.y - 1));
+    for (int i = 0; i < ol.y; ++i) {
+        const float3 b = f3(__ldg(cv + i));
+        const float3 e = b - a, q = P - a;
+        const float s = dot(cross(e, q), nf);
+        if (fabsf(s) > 1e-5f * sqrtf(dot(e, e)) * (pn + fabsf(q.x) + fabsf(q.y) + fabsf(q.z))) {
+            if (s < 0.0f) return false;
+        } else {
+            unsure = true;
+        }
+        a = b;
+    }
+    if (!unsure) return true;
+    const Plane64 pl = S.planes_d[f];
+    const dvec3 n = dv(pl.x, pl.y, pl.z);
+    float4 a4 = __ldg(cv + ol.y - 1);
+    dvec3 ad = dv(a4.x, a4.y, a4.z);
+    for (int i = 0; i < ol.y; ++i) {
+        const float4 b4 = __ldg(cv + i);
+        const dvec3 bd = dv(b4.x, b4.y, b4.z);
+        if (ddot(dcross(bd - ad, p - ad), n) < 0.0) return false;
+        ad = bd;
+    }
+    return true;
+}
+
 __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p) {
+    const int2 ol = __ldg(S.face_outline + f);
+    if (ol.y > 0) return point_in_outline(S, f, ol, p);
     const float3 nf = f3(__ldg(S.planes + f));   // the FP64 normal rounded to FP32
     const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
     const float tol = 1e-6f * (fabsf(px) + fabsf(py) + fabsf(pz)) + 1e-6f;

@@ -60,6 +60,9 @@ struct SceneDev {
     const float *face_eps;    // per face relative permittivity (<= 0: perfect reflector)
     const int *face_tri_off;  // CSR over faces -> triangle indices (BVH order)
     const int *face_tri_idx;
+    const int2 *face_outline; // per face (first corner, count) of its convex outline, count 0:
+                              // the face is tested triangle by triangle (build_face_outlines)
+    const float4 *outline_v;  // outline corners, counter-clockwise about the face normal
     int nt, nf, nnodes;
     float tmin;               // hits need t > tmin (1e-7 x scene diagonal)
     // wedges (order-1 diffraction): per wedge 4 float4 in wedge-id order,
@@ -215,6 +218,10 @@ void build_lattice_tables(int n, std::vector<float4> &ico, std::vector<int2> &ed
 int subray_pattern(int K, double *rho, double *phi, double *shrink);
 bool build_wedges(const float *verts, int64_t nv, const int32_t *tris, const int32_t *tri_face, int64_t nt, int nf,
                   std::vector<WedgeHost> &out);
+// Convex outlines of the faces whose triangles tile a convex polygon (host_faces.cpp).
+constexpr int kMaxOutline = 32;
+void build_face_outlines(const float *verts, const int32_t *tris, const int32_t *tri_face, int64_t nt, int nf,
+                         const Plane64 *planes, std::vector<int2> &outline, std::vector<float4> &corners);
 // Vertex / edge / face tables of the icosahedron (poly 20) or octahedron (poly 8).
 bool build_polyhedron(int poly, std::vector<float4> &v, std::vector<int2> &e, std::vector<int4> &f);
 

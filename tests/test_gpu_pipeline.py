@@ -209,6 +209,53 @@ def test_empty_scene_only_los(gpu_ctx, oracle_mod):
     _close(paths, rxs, scene)
 
 
+def test_nonconvex_face_validity(gpu_ctx, oracle_mod):
+    """§III.A validity on a face whose triangles do not tile a convex polygon (an L-shaped
+    wall of three squares, so the triangle-by-triangle point-in-face query runs rather
+    than the convex-outline test): every refined path's validity flag equals the oracle's
+    on the GPU's own direction, in the plain and batched forms, and paths over the L face
+    are both kept and rejected."""
+    b = scenes._Builder()
+    L = b.nf
+    b.nf += 1
+    for (y0, y1, z0, z1) in ((0, 3, 0, 1.5), (3, 6, 0, 1.5), (0, 3, 1.5, 3)):
+        b.quad((0, y0, z0), (0, y1, z0), (0, y0, z1), g=2, face=L)
+    b.quad((6, 0, 0), (6, 0, 3), (6, 6, 0))
+    b.quad((0, 0, 0), (0, 0, 3), (6, 0, 0))
+    b.quad((0, 6, 0), (6, 6, 0), (0, 6, 3))
+    b.quad((0, 0, 0), (6, 0, 0), (0, 6, 0))
+    b.quad((0, 0, 3), (0, 6, 3), (6, 0, 3))
+    sc = b.finish()
+    tx = np.array([[2.5, 3.0, 1.5]], np.float32)
+    rng = np.random.default_rng(3)
+    rx = np.stack([rng.uniform(0.5, 5.5, 12), rng.uniform(0.5, 5.5, 12), rng.uniform(0.3, 2.7, 12)], -1)
+    rx = rx.astype(np.float32)
+    scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx)
+    S = oracle_mod.Scene.from_generated(sc)
+    tl = oracle_mod.theta_launch(48)
+    flags = []
+    for mode in ("plain", "batch16", "batch1"):
+        gpu_ctx.launch(scene, tx, rxs, paths, 48, 2, rx_angle_scale=SQ3, sync=True)
+        if mode == "plain":
+            gpu_ctx.refine(scene, paths, 8, 9)
+        else:
+            gpu_ctx.batch_refine(scene, paths, 8, 9, lanes_per_path=int(mode[5:]))
+        got = gpu_ctx.query(paths)
+        flags.append({(int(r["rx"]), tuple(int(f) for f in r["faces"][: r["order"]])): int(r["valid"]) for r in got})
+        on_l = [0, 0]
+        for r in got:
+            faces = tuple(int(f) for f in r["faces"][: r["order"]])
+            R0 = max(tl, float(r["rough_err"]))
+            bound = oracle_mod.refined_err_bound(R0, 9, int(r["iters"])) if r["iters"] > 0 else 0.0
+            ev = oracle_mod.path_eval(S, tx[r["tx"]], rx[r["rx"]], faces, r["dir"], err_bound=bound)
+            assert bool(r["valid"]) == ev["valid"], (mode, faces)
+            if L in faces:
+                on_l[int(r["valid"])] += 1
+        assert on_l[0] >= 2 and on_l[1] >= 20, on_l
+    assert flags[0] == flags[1] == flags[2]
+    _close(paths, rxs, scene)
+
+
 def test_batched_and_per_pair_equal_plain(gpu_ctx, oracle_mod):
     """a9: the persistent work-queue form and the per-pair form give the plain form's
     results (same device arithmetic, different schedule).  With the early stop at 0.01 deg
