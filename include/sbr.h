@@ -216,7 +216,8 @@ sbr_status sbr_launch_get_stats(sbr_ctx *ctx, const sbr_paths *paths, sbr_launch
 typedef struct {
     int32_t max_iters;       /* iteration cap (>= 0) */
     int32_t subrays;         /* K in {6, 7, 9, 16} */
-    double target_err_rad;   /* stop once the error angle is <= this (<= 0: never early) */
+    double target_err_rad;   /* stop once the AOD error (the error angle) and the AOA error
+                                are both <= this (<= 0: never early) */
     double fp64_below_rad;   /* run an iteration in FP64 once the cone half-angle is below
                                 this (default 1e-5 when 0) */
     double freq_hz;          /* carrier for the power term (0: 2.4e9) */
@@ -228,9 +229,11 @@ typedef struct {
  * initial cone is centred on the path's rough launch direction with half-angle
  * max(theta_launch, rough error angle); each iteration traces K sub-rays through the
  * path's fixed face planes, keeps the one with the smallest error angle (Eq. 3) and
- * shrinks the cone.  Then the validity test (bounce points inside their faces, no
- * segment occluded) and the outputs (delay, AOD, AOA, power).  One thread per path,
- * static schedule. */
+ * shrinks the cone, until the iteration cap or, with a target, until the path's AOD and
+ * AOA errors both meet it (§III.B: iterate until the error satisfies the requirement;
+ * the AOA error is measured exactly in the unfolded space).  Then the validity test
+ * (bounce points inside their faces, no segment occluded) and the outputs (delay, AOD,
+ * AOA, power).  One thread per path, static schedule. */
 sbr_status sbr_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths, const sbr_refine_params *params);
 /* Same as sbr_refine restricted to the paths of one (tx, rx) pair: the per-pair form. */
 sbr_status sbr_refine_pair(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths, int32_t tx, int32_t rx,

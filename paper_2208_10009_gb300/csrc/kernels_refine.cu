@@ -370,9 +370,13 @@ __device__ __forceinline__ int iterate32(const UnfF &uf, int nk, int K, int off,
     float best = INFINITY, bdw = 0.0f;
     int bk = -1;
     float3 bd = cf;
+    // the patterns' sub-rays come ring by ring: one sine and cosine per ring radius
+    float rho = -1.0f, sa = 0.0f, ca = 1.0f;
     for (int k = 0; k < K; ++k) {
-        float sa, ca;
-        sincos_sub32(c_sub.rho[off + k] * Rf, sa, ca);
+        if (c_sub.rho[off + k] != rho) {
+            rho = c_sub.rho[off + k];
+            sincos_sub32(rho * Rf, sa, ca);
+        }
         float3 dk = cf * ca + (u * c_sub.cphi[off + k] + v * c_sub.sphi[off + k]) * sa;
         float dw = 0.0f;
         float key = key32(uf, nk, dk, dw);
@@ -399,9 +403,12 @@ __device__ __forceinline__ int iterate64(const UnfD &ud, int nk, int K, int off,
     double best = INFINITY, bdw = 0.0;
     int bk = -1;
     dvec3 bd = c;
+    double rho = -1.0, sa = 0.0, ca = 1.0;
     for (int k = 0; k < K; ++k) {
-        double sa, ca;
-        sincos_sub(c_sub.rho_d[off + k] * R, sa, ca);
+        if (c_sub.rho_d[off + k] != rho) {
+            rho = c_sub.rho_d[off + k];
+            sincos_sub(rho * R, sa, ca);
+        }
         dvec3 dk = c * ca + (u * c_sub.cphi_d[off + k] + v * c_sub.sphi_d[off + k]) * sa;
         double dw = 0.0;
         double key = key64(ud, nk, dk, dw);
