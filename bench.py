@@ -190,7 +190,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ray-bounces/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {k: v for k, v in WORKLOAD.items()},
+           "config": {k: v for k, v in WORKLOAD.items() if k != "gen"},
            "cpu_baseline": {"value": value, "unit": "ray-bounces/s", "cores": cores, "kind": "oracle",
                             "sample": f"every {stride}th ray id per step ({nr // max(args.steps, 1)} rays), "
                                       f"brute-force FP64 trace + refine"},

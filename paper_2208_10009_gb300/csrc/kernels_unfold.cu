@@ -67,6 +67,38 @@ __device__ __forceinline__ float3 apply_AT(const SceneDev &S, const UnfoldPath &
     return x;
 }
 
+// The linear part of the unfolding as a matrix, A = H_1 ... H_k (row-major m[9]), built
+// by right-multiplying the reflections H = I - 2 n n^T in path order: A H = A - 2 (A n) n^T.
+// It runs beside the point chains, so the adjoint's linear pull-backs become 3 x 3
+// products instead of further mirror chains after them.
+__device__ __forceinline__ void build_A(const SceneDev &S, const UnfoldPath &u, float m[9]) {
+    m[0] = 1.0f; m[1] = 0.0f; m[2] = 0.0f;
+    m[3] = 0.0f; m[4] = 1.0f; m[5] = 0.0f;
+    m[6] = 0.0f; m[7] = 0.0f; m[8] = 1.0f;
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j) {
+        if (j >= u.k) break;
+        const float3 n = f3(__ldg(S.planes + u.faces[j]));
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const float an = 2.0f * fmaf(m[3 * r], n.x, fmaf(m[3 * r + 1], n.y, m[3 * r + 2] * n.z));
+            m[3 * r] = fmaf(-an, n.x, m[3 * r]);
+            m[3 * r + 1] = fmaf(-an, n.y, m[3 * r + 1]);
+            m[3 * r + 2] = fmaf(-an, n.z, m[3 * r + 2]);
+        }
+    }
+}
+
+__device__ __forceinline__ float3 mul_A(const float m[9], float3 x) {
+    return make_float3(fmaf(m[0], x.x, fmaf(m[1], x.y, m[2] * x.z)), fmaf(m[3], x.x, fmaf(m[4], x.y, m[5] * x.z)),
+                       fmaf(m[6], x.x, fmaf(m[7], x.y, m[8] * x.z)));
+}
+
+__device__ __forceinline__ float3 mul_AT(const float m[9], float3 x) {
+    return make_float3(fmaf(m[0], x.x, fmaf(m[3], x.y, m[6] * x.z)), fmaf(m[1], x.x, fmaf(m[4], x.y, m[7] * x.z)),
+                       fmaf(m[2], x.x, fmaf(m[5], x.y, m[8] * x.z)));
+}
+
 __device__ __forceinline__ void angles(float3 w, float &az, float &el) {
     az = atan2f(w.y, w.x);
     el = atan2f(w.z, sqrtf(w.x * w.x + w.y * w.y));
@@ -88,6 +120,8 @@ __global__ void unfold_fwd_kernel(UnfoldArgs a) {
             for (int j = 0; j < 8; ++j) a.out[8 * i + j] = __int_as_float(0x7fc00000);
             continue;
         }
+        float mA[9];
+        build_A(a.scene, u, mA);
         float3 rxp = apply_A(a.scene, u, u.rx, true);
         float3 w = rxp - u.tx;
         float se, ce, sa, ca;
@@ -95,7 +129,7 @@ __global__ void unfold_fwd_kernel(UnfoldArgs a) {
         sincosf(u.az, &sa, &ca);
         float3 d = make_float3(ce * ca, ce * sa, se);
         float3 m = w - d * dot(w, d);
-        float3 miss = apply_AT(a.scene, u, m, false);
+        float3 miss = mul_AT(mA, m);
         float3 txk = apply_AT(a.scene, u, u.tx, true);
         float3 v = txk - u.rx;
         float *o = a.out + 8 * i;
@@ -118,8 +152,21 @@ __global__ void unfold_bwd_kernel(UnfoldArgs a) {
             a.grad_az_el[2 * i] = a.grad_az_el[2 * i + 1] = nan;
             continue;
         }
-        const float *g = a.grad_out + 8 * i;
+        // the row of 8 output gradients: two 16-byte loads when the array is 16-byte
+        // aligned (every row then is), else eight 4-byte loads
+        float g[8];
+        if ((reinterpret_cast<uintptr_t>(a.grad_out) & 15) == 0) {
+            const float4 g0 = __ldg(reinterpret_cast<const float4 *>(a.grad_out) + 2 * i);
+            const float4 g1 = __ldg(reinterpret_cast<const float4 *>(a.grad_out) + 2 * i + 1);
+            g[0] = g0.x; g[1] = g0.y; g[2] = g0.z; g[3] = g0.w;
+            g[4] = g1.x; g[5] = g1.y; g[6] = g1.z; g[7] = g1.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) g[j] = __ldg(a.grad_out + 8 * i + j);
+        }
         // recompute the forward quantities
+        float m[9];
+        build_A(a.scene, u, m);
         float3 rxp = apply_A(a.scene, u, u.rx, true);
         float3 w = rxp - u.tx;
         float se, ce, sa, ca;
@@ -132,7 +179,7 @@ __global__ void unfold_bwd_kernel(UnfoldArgs a) {
         float3 v = txk - u.rx;
         float wd = dot(w, d);
         // miss = A^T (w - (w.d) d): pull g_miss back into unfolded space
-        float3 gm = apply_A(a.scene, u, make_float3(g[0], g[1], g[2]), false);
+        float3 gm = mul_A(m, make_float3(g[0], g[1], g[2]));
         float gmd = dot(gm, d);
         float3 gw = gm - d * gmd;
         float3 gd = (gm * wd + w * gmd) * -1.0f;
@@ -146,8 +193,8 @@ __global__ void unfold_bwd_kernel(UnfoldArgs a) {
         // AOA angles of v = A^T Tx + b0 - Rx
         angles_grad(v, gaz, gel);
         float3 gv = gaz * g[6] + gel * g[7];
-        float3 gtx = gw * -1.0f + apply_A(a.scene, u, gv, false);
-        float3 grx = apply_AT(a.scene, u, gw, false) - gv;
+        float3 gtx = gw * -1.0f + mul_A(m, gv);
+        float3 grx = mul_AT(m, gw) - gv;
         a.grad_tx[3 * i] = gtx.x;
         a.grad_tx[3 * i + 1] = gtx.y;
         a.grad_tx[3 * i + 2] = gtx.z;
