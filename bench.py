@@ -59,25 +59,38 @@ TRACE_SOURCES = ["paper_2208_10009_gb300/csrc/kernels_trace.cu", "paper_2208_100
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "trace_kernel_traffic.json")
 
 
-def trace_source_hash() -> str:
+UNFOLD_SOURCES = ["paper_2208_10009_gb300/csrc/kernels_unfold.cu", "paper_2208_10009_gb300/csrc/sbr_device.cuh",
+                  "paper_2208_10009_gb300/csrc/sbr_internal.h"]
+UNFOLD_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "unfold_bwd_traffic.json")
+
+
+def source_hash(sources) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in TRACE_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def trace_traffic():
-    """DRAM bytes per trace launch from the committed ncu record, or None when the kernel
-    sources have changed since it was captured."""
+def trace_source_hash() -> str:
+    return source_hash(TRACE_SOURCES)
+
+
+def recorded_traffic(path, sources):
+    """DRAM bytes per launch from a committed ncu record, or None when the kernel sources
+    have changed since it was captured."""
     try:
-        rec = json.load(open(TRAFFIC_FILE))
+        rec = json.load(open(path))
     except Exception:
         return None, None
-    if rec.get("source_sha256") != trace_source_hash():
+    if rec.get("source_sha256") != source_hash(sources):
         return None, rec
     return rec["dram_bytes_per_launch"], rec
+
+
+def trace_traffic():
+    return recorded_traffic(TRAFFIC_FILE, TRACE_SOURCES)
 
 
 def _peaks():
@@ -427,6 +440,7 @@ def run_grad(args):
     bwd_ms = float(np.median(times))
     peaks, src = _peaks()
     bwd_bytes = P * (100 + 32)
+    traffic, traffic_rec = recorded_traffic(UNFOLD_TRAFFIC_FILE, UNFOLD_SOURCES)
     print(json.dumps({"metric": "unfolding forward + adjoint paths/s", "value": P / (ms / 1e3), "unit": "paths/s",
                       "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -435,7 +449,9 @@ def run_grad(args):
                       "roofline": {"bound": "hbm", "kernel": "unfold_bwd_kernel", "achieved": bwd_bytes / (bwd_ms / 1e3) / 1e9,
                                    "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                                    "frac": bwd_bytes / (bwd_ms / 1e3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
-                                   "traffic": None, "peak_source": src, "bwd_ms": bwd_ms}}), flush=True)
+                                   "traffic": traffic,
+                                   "traffic_source": None if traffic is None else traffic_rec.get("capture"),
+                                   "peak_source": src, "bwd_ms": bwd_ms}}), flush=True)
     for h in (paths, rxs, scene):
         h.close()
     ctx.close()
