@@ -140,6 +140,48 @@ def test_wedge_refinement_eq10_and_floor(oracle_mod):
         assert r["err"] < 1e-13
 
 
+def test_wedge_early_stop_on_aod_and_aoa(oracle_mod):
+    """§III.B early stop for diffraction paths: refinement stops once the AOD and the AOA
+    (from Rx to the diffraction point) are both within the target, checked against the
+    exact diffraction path (Fermat point on the edge): at the stop both hold, one
+    iteration earlier at least one did not; and for some wedge the AOD alone meets the
+    target before the AOA does."""
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4), bottom=False))
+    ab, fc = oracle_mod.wedges(S)
+    rng = np.random.default_rng(5)
+    tx, rx = np.array([-5.0, 1.5, 1.0]), np.array([1.5, -0.6, 1.2])
+    tl = oracle_mod.theta_launch(32)
+    target = np.radians(0.01)
+
+    def dir_of(az, el):
+        return np.array([np.cos(el) * np.cos(az), np.cos(el) * np.sin(az), np.sin(el)])
+
+    def errors(w, d):
+        ev = oracle_mod.wedge_eval(S, tx, rx, w, d)
+        im = oracle_mod.wedge_image(S, tx, rx, w)
+        return _ang(d, im["aod_dir"]), _ang(dir_of(*ev["aoa"]), dir_of(*im["aoa"]))
+
+    checked = aod_first = 0
+    for w in range(len(fc)):
+        im = oracle_mod.wedge_image(S, tx, rx, w)
+        if im["status"] < 0:
+            continue
+        c0 = im["aod_dir"] + rng.normal(size=3) * 0.3 * tl
+        c0 /= np.linalg.norm(c0)
+        R0 = max(tl, _ang(c0, im["aod_dir"]))
+        r = oracle_mod.refine_wedge(S, tx, rx, w, c0, R0, 9, 20, target)
+        assert r["iters"] < 20
+        aod, aoa = errors(w, r["dir"])
+        assert aod <= target and aoa <= target * (1 + 1e-9)
+        if r["iters"] > 0:
+            q = oracle_mod.refine_wedge(S, tx, rx, w, c0, R0, 9, r["iters"] - 1, target)
+            aod1, aoa1 = errors(w, q["dir"])
+            assert aod1 > target or aoa1 > target
+            aod_first += aod1 <= target
+        checked += 1
+    assert checked >= 6 and aod_first >= 1
+
+
 def test_rough_records_error_angle(oracle_mod):
     """Every rough diffraction record's error angle is the angle between its ray and the
     direction to the receiver rotated about the edge (computed here with Rodrigues'
