@@ -781,13 +781,14 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
     }
 }
 
-// a9: persistent work-queue form.  A group of G lanes (G = 8, 16 or 32) owns one path at a
-// time: lane l evaluates the sub-rays k = l, l + G, ... of each iteration and the group
-// takes the argmin with shuffles (lowest k on ties, as in the plain form).  When a path is
-// finished (iteration cap, target reached, stalled, or all sub-rays invalid) the group
-// takes the next path index from the device queue head with one atomic, so paths that stop
-// early free their group at once.  The validity test and outputs follow in
-// batch_finalize_kernel.
+// a9: persistent work-queue form.  A group of G lanes (G = 1, 8, 16 or 32) owns one path at
+// a time: lane l evaluates the sub-rays k = l, l + G, ... of each iteration and the group
+// takes the argmin with shuffles (lowest k on ties, as in the plain form; one lane runs
+// the plain form's iterate32).  When a path is finished (iteration cap, target reached,
+// stalled, or all sub-rays invalid) the group takes the next path index from the device
+// queue head with one atomic, so paths that stop early free their group at once.  With
+// many paths, a path whose cone falls below the FP64 threshold moves on to
+// batch_refine64_kernel; the validity test and outputs follow in batch_finalize_kernel.
 template <int G>
 __device__ __forceinline__ void group_argmin(float &e, int &k, unsigned gmask) {
 #pragma unroll
