@@ -248,12 +248,13 @@ typedef struct {
 /* a9 -- batched form of a6-a8: one persistent launch refines all paths of all (Tx, Rx)
  * pairs.  A group of lanes_per_path lanes owns one path: its lanes evaluate the K
  * sub-rays of an iteration in parallel (one lane: all K in turn, the form for many
- * paths); a group that finishes a path (iteration cap,
- * target reached, stalled) takes the next one from a device work queue (atomic head), so
- * uneven iteration counts do not idle the GPU.  A second launch runs the validity test and
- * outputs (one thread per path when there are many, one warp per path when there are
- * few).  Results equal sbr_refine's.  Capturable in a CUDA graph (no host
- * synchronisation, no allocation). */
+ * paths); a group that finishes a path (iteration cap, target reached, stalled) takes the
+ * next one from a device work queue (atomic head), so uneven iteration counts do not idle
+ * the GPU.  With many paths (and always with one lane per path) a launch before it unfolds
+ * every path's planes one path per thread and a launch after it runs the FP64 iterations
+ * one path per thread.  A last launch runs the validity test and outputs (one thread per
+ * path when there are many, one warp per path when there are few).  Results equal
+ * sbr_refine's.  Capturable in a CUDA graph (no host synchronisation, no allocation). */
 sbr_status sbr_batch_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths,
                             const sbr_refine_params *params, const sbr_batch_config *cfg);
 
