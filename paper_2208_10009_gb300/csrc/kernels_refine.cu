@@ -203,6 +203,10 @@ __device__ __forceinline__ float key32(const UnfF &u, int k, float3 d, float &dw
     return dot(c, c);
 }
 
+// The FP64 form takes its sign tests on the doubles' bits with integer instructions: on
+// GB300 a double compare occupies the 1/64-rate FP64 pipe like an FMA does.  den != 0 is
+// (bits << 1) != 0, and T_j - T_{j-1} > 0 is x != 0 with the sign bits of x, den and
+// T_{j-1}'s denominator XOR-ing to 0 (the same decisions as key32's compares).
 __device__ __forceinline__ double key64(const UnfD &u, int k, dvec3 d, double &dw) {
     double pn = 0.0, pd = 1.0;
 #pragma unroll
@@ -210,16 +214,17 @@ __device__ __forceinline__ double key64(const UnfD &u, int k, dvec3 d, double &d
         if (j >= k) break;
         const D4 P = u.p[j];
         const double den = fma(P.x, d.x, fma(P.y, d.y, P.z * d.z));
-        if (den == 0.0) return INFINITY;
+        const long long bd = __double_as_longlong(den);
+        if ((bd << 1) == 0) return INFINITY;
         const double x = fma(P.w, pd, -pn * den);
-        const bool same = (den > 0.0) == (pd > 0.0);
-        if (!(same ? x > 0.0 : x < 0.0)) return INFINITY;
+        const long long bx = __double_as_longlong(x);
+        if ((bx << 1) == 0 || (bx ^ bd ^ __double_as_longlong(pd)) < 0) return INFINITY;
         pn = P.w;
         pd = den;
     }
     const dvec3 W = dv(u.w.x, u.w.y, u.w.z);
     dw = ddot(d, W);
-    if (!(dw > 0.0)) return INFINITY;
+    if (__double_as_longlong(dw) <= 0) return INFINITY;   // dw > 0 (a positive double's bits are > 0)
     const dvec3 c = dcross(d, W);
     return ddot(c, c);
 }
@@ -412,7 +417,8 @@ __device__ __forceinline__ int iterate64(const UnfD &ud, int nk, int K, int off,
         dvec3 dk = c * ca + (u * c_sub.cphi_d[off + k] + v * c_sub.sphi_d[off + k]) * sa;
         double dw = 0.0;
         double key = key64(ud, nk, dk, dw);
-        if (key < best) {
+        // key < best, both >= 0 (or +inf): their bits order like the values
+        if (__double_as_longlong(key) < __double_as_longlong(best)) {
             best = key;
             bdw = dw;
             bk = k;
