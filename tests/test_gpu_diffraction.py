@@ -130,18 +130,20 @@ def test_early_stop_diffraction(gpu_ctx, oracle_mod, block):
     sc, tx, rx, n, S, scene, rxs, paths, ora, dr = block
     cap, target = 12, np.radians(0.01)
     res = []
-    for mode in ("plain", "batch"):
+    for mode in ("plain", "batch", "batch1"):
         gpu_ctx.launch(scene, tx, rxs, paths, n, 2, rx_angle_scale=SQ3, sync=True, diffraction=True)
         if mode == "plain":
             gpu_ctx.refine(scene, paths, cap, 9, target=target)
         else:
-            gpu_ctx.batch_refine(scene, paths, cap, 9, target=target)
+            gpu_ctx.batch_refine(scene, paths, cap, 9, target=target, lanes_per_path=1 if mode == "batch1" else 0)
         got = gpu_ctx.query(paths)
         res.append({(int(g["tx"]), int(g["rx"]), int(g["order"]), tuple(int(f) for f in g["faces"][: g["order"]])): g
                     for g in got})
-    assert set(res[0]) == set(res[1])
-    for k, g in res[0].items():
-        assert g["iters"] == res[1][k]["iters"] and ang(g["dir"], res[1][k]["dir"]) < 1e-9
+    for other in res[1:]:
+        assert set(res[0]) == set(other)
+        for k, g in res[0].items():
+            assert g["iters"] == other[k]["iters"] and g["valid"] == other[k]["valid"]
+            assert ang(g["dir"], other[k]["dir"]) < 1e-9
     tl = oracle_mod.theta_launch(n)
     near = early = early_diff = 0
     for (t, r, k, faces), g in res[1].items():
@@ -163,6 +165,33 @@ def test_early_stop_diffraction(gpu_ctx, oracle_mod, block):
         early += 1
         early_diff += diff
     assert near <= 0.1 * len(res[1]) and early_diff > 10
+
+
+def test_fp64_tail_with_diffraction(gpu_ctx, block):
+    """The one-lane batched form always hands cones below 1e-5 rad to the thread-per-path
+    FP64 tail kernel; with 12 iterations (no early stop) reflection and diffraction paths
+    reach it, and the results equal the plain form's."""
+    sc, tx, rx, n, S, scene, rxs, paths, ora, dr = block
+    out = []
+    for mode in ("plain", "batch1"):
+        gpu_ctx.launch(scene, tx, rxs, paths, n, 2, rx_angle_scale=SQ3, sync=True, diffraction=True)
+        if mode == "plain":
+            gpu_ctx.refine(scene, paths, 12, 9)
+        else:
+            gpu_ctx.batch_refine(scene, paths, 12, 9, lanes_per_path=1)
+        got = gpu_ctx.query(paths)
+        out.append({(int(g["tx"]), int(g["rx"]), int(g["order"]), tuple(int(f) for f in g["faces"][: g["order"]])): g
+                    for g in got})
+    a, b = out
+    assert set(a) == set(b)
+    fp64_diff = 0
+    for k, g in a.items():
+        h = b[k]
+        assert g["iters"] == h["iters"] and g["valid"] == h["valid"] and g["flags"] == h["flags"]
+        assert ang(g["dir"], h["dir"]) < 1e-12
+        assert abs(g["delay"] - h["delay"]) <= 1e-12 * g["delay"]
+        fp64_diff += bool(g["flags"] & B.PATH_FP64) and bool(g["flags"] & B.PATH_DIFFRACTED)
+    assert fp64_diff > 5
 
 
 def test_diffraction_leaves_reflections_alone(gpu_ctx, block):
