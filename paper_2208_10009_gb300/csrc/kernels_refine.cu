@@ -787,6 +787,22 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
     }
 }
 
+// Lists path pi in its order group for batch_finalize_kernel (group offsets from
+// batch_unfold_kernel's counts), so that a warp there holds paths of one order.  Inside the
+// group, paths whose error meets the convergence bound 2 R + 1e-7 (the validity test's
+// condition; R is the cone radius after the iterations, here only an ordering hint) fill it
+// from the front and the others, which the validity test rejects at once, from the back:
+// a warp's lanes then run their BVH queries, or skip them, together.
+__device__ __forceinline__ void list_for_finalize(const RefineArgs &A, const PathGeo &g, long long pi, double err,
+                                                  double R) {
+    const int grp = order_group(g);
+    unsigned long long at = 0;
+    for (int b = 0; b < grp; ++b) at += A.order_cnt[b];
+    if (err <= 2.0 * R + 1e-7) at += atomicAdd(A.order_cnt + 16 + grp, 1ULL);
+    else at += A.order_cnt[grp] - 1ULL - atomicAdd(A.order_cnt + 48 + grp, 1ULL);
+    A.order_idx[at] = (int)pi;
+}
+
 // a9: persistent work-queue form.  A group of G lanes (G = 1, 8, 16 or 32) owns one path at
 // a time: lane l evaluates the sub-rays k = l, l + G, ... of each iteration and the group
 // takes the argmin with shuffles (lowest k on ties, as in the plain form; one lane runs
@@ -1087,15 +1103,7 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
             p.dir[1] = c.y;
             p.dir[2] = c.z;
             p.err = error_angle(key, dw, keyf, dwf, fp64);
-            if (prebuilt) {
-                // list the path in its order group (group offsets from batch_unfold_kernel's
-                // counts), so that the finalize kernel's warps see paths of one order
-                const int grp = order_group(g);
-                unsigned long long at = 0;
-                for (int b = 0; b < grp; ++b) at += A.order_cnt[b];
-                at += atomicAdd(A.order_cnt + 16 + grp, 1ULL);
-                A.order_idx[at] = (int)pi;
-            }
+            if (prebuilt) list_for_finalize(A, g, pi, p.err, (double)Rf);
             // iteration results; the validity test and outputs follow in batch_finalize_kernel
             sbr_path_record *dst = A.paths + pi;
             dst->iters = p.iters;
@@ -1177,17 +1185,14 @@ __global__ void __launch_bounds__(128) batch_refine64_kernel(RefineArgs A) {
         else if (it < A.max_iters && !(fp64 ? reached(A, g, ud, c, key, dw) : reached32(A, g, uf, cf, keyf, dwf)))
             flags |= SBR_PATH_STALLED;
         if (!fp64) c = dv(cf.x, cf.y, cf.z);
-        const int grp = order_group(g);
-        unsigned long long at = 0;
-        for (int b = 0; b < grp; ++b) at += A.order_cnt[b];
-        at += atomicAdd(A.order_cnt + 16 + grp, 1ULL);
-        A.order_idx[at] = (int)pi;
+        const double err = error_angle(key, dw, keyf, dwf, fp64);
+        list_for_finalize(A, g, pi, err, R);
         sbr_path_record *dst = A.paths + pi;
         dst->iters = it;
         dst->dir[0] = c.x;
         dst->dir[1] = c.y;
         dst->dir[2] = c.z;
-        dst->err = error_angle(key, dw, keyf, dwf, fp64);
+        dst->err = err;
         dst->flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
     }
 }
@@ -1302,7 +1307,7 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&unf_blocks, batch_unfold_kernel, 128, 0);
         if (unf_blocks < 1) unf_blocks = 1;
     }
-    e = cudaMemsetAsync(a.order_cnt, 0, 48 * sizeof(unsigned long long), s);
+    e = cudaMemsetAsync(a.order_cnt, 0, 64 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     batch_unfold_kernel<<<sms * unf_blocks, 128, 0, s>>>(a);
     switch (a.chunk) {

@@ -171,8 +171,8 @@ struct sbr_paths {
     sbr_path_record *paths = nullptr;
     float4 *unf = nullptr;                 // batched refinement: kUnfStride float4 per path
     int *order_idx = nullptr;              // batched refinement: path indices grouped by order
-    unsigned long long *order_cnt = nullptr;   // [0, 10): paths per group, [16, 26) and [32, 42): fill
-                                               // cursors of order_idx and fp64_idx
+    unsigned long long *order_cnt = nullptr;   // [0, 10): paths per group; fill cursors: [16, 26) order_idx
+                                               // from the front, [48, 58) from the back, [32, 42) fp64_idx
     int *fp64_idx = nullptr;               // batched refinement: paths handed to the FP64 tail
     unsigned long long *table = nullptr;   // dedup hash table: 2 x u64 per slot (key, value)
     int64_t table_slots = 0;
@@ -304,8 +304,9 @@ struct RefineArgs {
     float4 *unf;              // batched form, per path (kUnfStride float4): FP32 unfolded planes
                               // [0, kMaxOrder), W at kMaxOrder, rough direction at kMaxOrder + 1
     int *order_idx;           // batched form: path indices grouped by order (diffraction last)
-    unsigned long long *order_cnt;   // batched form: group sizes [0, 10), fill cursors [16, 26) of
-                                     // order_idx and [32, 42) of fp64_idx
+    unsigned long long *order_cnt;   // batched form: group sizes [0, 10), fill cursors of order_idx
+                                     // ([16, 26) from the front, [48, 58) from the back) and
+                                     // [32, 42) of fp64_idx
     int *fp64_idx;            // batched form: paths whose FP64 iterations run in the tail kernel,
                               // grouped by order like order_idx
     int chunk;                // lanes per path in the batched kernel (8, 16, 32)
