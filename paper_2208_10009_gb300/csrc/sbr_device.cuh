@@ -212,7 +212,10 @@ __device__ __forceinline__ void cswap(float &da, int &ra, float &db, int &rb) {
     ra = r;
 }
 
-// Closest hit through the 4-wide BVH.  Per node, slab tests of the four child boxes as
+// Closest hit through the 4-wide BVH.  The walk descends inner nodes in an inner loop and
+// tests a leaf once it reaches one ("while-while"): a warp then runs the leaf branch only
+// when its lanes stand at leaves, not on every step where one lane does.  Per node, slab
+// tests of the four child boxes as
 // t = plane * (1/d) - o * (1/d), the near / far planes picked by the ray's direction
 // signs (so no per-axis min/max), two children per packed FMA and three-input min/max;
 // the hit children are sorted by entry distance, the nearest is visited next and the
@@ -228,7 +231,8 @@ __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, 
     int best = -1, bface = 0x7fffffff;
     const float oix = r.o.x * r.inv.x, oiy = r.o.y * r.inv.y, oiz = r.o.z * r.inv.z;
     for (;;) {
-        if (!is_leaf(node)) {
+        bool done = false;
+        while (!is_leaf(node)) {
             ++nodes_visited;
             const float4 *nd = S.nodes4 + 8 * (size_t)node;
             float4 nxv = __ldg(nd + r.nx), fxv = __ldg(nd + 1 - r.nx);
@@ -262,7 +266,14 @@ __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, 
                 node = pick == 0 ? refs.x : (pick == 1 ? refs.y : (pick == 2 ? refs.z : refs.w));
                 continue;
             }
-        } else {
+            if (sp == 0) {
+                done = true;
+                break;
+            }
+            node = stack[--sp];
+        }
+        if (done) break;
+        {
             int first = leaf_first(node), cnt = leaf_count(node);
             for (int i = first; i < first + cnt; ++i) {
                 const float4 *t = S.tris + 3 * (size_t)i;
@@ -328,14 +339,16 @@ __device__ __forceinline__ bool any_hit(const SceneDev &S, const RayPre &r, floa
 
 // Any hit of the segment o + t d, t in (tmin, tmax), ignoring faces fa and fb, over the
 // 4-wide BVH (the same triangles and the same triangle test as any_hit, so the same
-// answer, with fewer node visits).
+// answer, with fewer node visits); inner nodes and leaves in nested loops as in
+// closest_hit4.
 __device__ __forceinline__ bool any_hit4(const SceneDev &S, const RayPre &r, float tmin, float tmax, int fa, int fb) {
     int stack[kStack4];
     int sp = 0;
     int node = 0;
     const float oix = r.o.x * r.inv.x, oiy = r.o.y * r.inv.y, oiz = r.o.z * r.inv.z;
     for (;;) {
-        if (!is_leaf(node)) {
+        bool done = false;
+        while (!is_leaf(node)) {
             const float4 *nd = S.nodes4 + 8 * (size_t)node;
             float4 nxv = __ldg(nd + r.nx), fxv = __ldg(nd + 1 - r.nx);
             float4 nyv = __ldg(nd + 2 + r.ny), fyv = __ldg(nd + 3 - r.ny);
@@ -365,7 +378,14 @@ __device__ __forceinline__ bool any_hit4(const SceneDev &S, const RayPre &r, flo
                 node = next;
                 continue;
             }
-        } else {
+            if (sp == 0) {
+                done = true;
+                break;
+            }
+            node = stack[--sp];
+        }
+        if (done) break;
+        {
             int first = leaf_first(node), cnt = leaf_count(node);
             for (int i = first; i < first + cnt; ++i) {
                 const float4 *t = S.tris + 3 * (size_t)i;
