@@ -251,9 +251,12 @@ __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, 
             float dist[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
+                // hit iff tn <= tf (1 + 5e-7): tn, or +inf on a miss, as an FMA, a product
+                // with +inf (-inf or NaN on a hit) and a max, keeping the compare and select
+                // off the busier ALU pipe
                 float tn = max3f(tnx[c], tny[c], fmaxf(tnz[c], tmin));
-                float tf = min3f(tfx[c], tfy[c], fminf(tfz[c], tbest)) * 1.0000005f;
-                dist[c] = tn <= tf ? tn : INFINITY;
+                float tf = min3f(tfx[c], tfy[c], fminf(tfz[c], tbest));
+                dist[c] = fmaxf(tn, fmaf(-tf, 1.0000005f, tn) * INFINITY);
             }
             float d0 = dist[0], d1 = dist[1], d2 = dist[2], d3 = dist[3];
             float dmin = fminf(min3f(d0, d1, d2), d3);
