@@ -128,6 +128,18 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
                             const int32_t *tri_face, int64_t nt, const float *face_eps, int32_t nf,
                             sbr_scene **out);
 sbr_status sbr_scene_destroy(sbr_ctx *ctx, sbr_scene *scene);
+/* Host only (no device, no context): the convex outlines the validity test's point-in-face
+ * query uses (§III.A: each refined bounce point must lie on its face).  corners (nf int32,
+ * host) receives, per face, the corner count of the convex polygon its triangles tile
+ * exactly (such a face is tested against that polygon's edges), or 0 when they do not
+ * (the face is tested triangle by triangle through the BVH).  A face's plane comes from
+ * its first triangle, as in sbr_scene_upload; the triangles tile the hull when, on that
+ * plane, each turns like the normal, each edge occurs at most once per direction, and the
+ * edges without a reverse twin and the triangles add up to the hull's perimeter and area
+ * (relative 1e-9).  Same arrays as sbr_scene_upload; SBR_EINVAL for null or negative
+ * sizes, SBR_EDEGENERATE for ids out of range or zero-area triangles. */
+sbr_status sbr_face_outline_corners(const float *verts, int64_t nv, const int32_t *tris, const int32_t *tri_face,
+                                    int64_t nt, int32_t nf, int32_t *corners);
 sbr_status sbr_scene_get_info(const sbr_scene *scene, sbr_scene_info *out);
 /* The scene's wedges, where rays diffract (§III.A, Fig. 4; the paper does not define a
  * wedge, this library's reading): a side shared by two faces -- the same segment, with

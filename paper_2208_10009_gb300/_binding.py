@@ -89,6 +89,7 @@ SIGNATURES = {
     "sbr_num_rays_launcher": (_i64, [_i32, _i32]),
     "sbr_scene_upload": (_i32, [_vp, _pf, _i64, _pi32, _pi32, _i64, _pf, _i32, _c.POINTER(_vp)]),
     "sbr_scene_destroy": (_i32, [_vp, _vp]),
+    "sbr_face_outline_corners": (_i32, [_pf, _i64, _pi32, _pi32, _i64, _i32, _pi32]),
     "sbr_scene_get_info": (_i32, [_vp, _c.POINTER(SceneInfo)]),
     "sbr_scene_wedges": (_i32, [_vp, _vp, _vp, _i64, _c.POINTER(_i64)]),
     "sbr_rx_upload": (_i32, [_vp, _vp, _i32, _c.POINTER(_vp)]),

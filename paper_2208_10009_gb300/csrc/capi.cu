@@ -506,6 +506,36 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     return SBR_OK;
 }
 
+sbr_status sbr_face_outline_corners(const float *verts, int64_t nv, const int32_t *tris, const int32_t *tri_face,
+                                    int64_t nt, int32_t nf, int32_t *corners) {
+    if (nv < 0 || nt < 0 || nf < 0 || (nf > 0 && !corners) || (nt > 0 && (!verts || !tris || !tri_face)))
+        return SBR_EINVAL;
+    // face planes from each face's first triangle, as in sbr_scene_upload
+    std::vector<Plane64> planes((size_t)std::max(nf, 1), Plane64{0, 0, 0, 0});
+    std::vector<char> seen((size_t)std::max(nf, 1), 0);
+    for (int64_t t = 0; t < nt; ++t) {
+        int ia = tris[3 * t], ib = tris[3 * t + 1], ic = tris[3 * t + 2], f = tri_face[t];
+        if (ia < 0 || ib < 0 || ic < 0 || ia >= nv || ib >= nv || ic >= nv || f < 0 || f >= nf)
+            return SBR_EDEGENERATE;
+        const float *A = verts + 3 * ia, *B = verts + 3 * ib, *C = verts + 3 * ic;
+        double e1[3] = {(double)B[0] - A[0], (double)B[1] - A[1], (double)B[2] - A[2]};
+        double e2[3] = {(double)C[0] - A[0], (double)C[1] - A[1], (double)C[2] - A[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(len > 0.0)) return SBR_EDEGENERATE;
+        if (!seen[f]) {
+            seen[f] = 1;
+            double u[3] = {n[0] / len, n[1] / len, n[2] / len};
+            planes[f] = Plane64{u[0], u[1], u[2], u[0] * A[0] + u[1] * A[1] + u[2] * A[2]};
+        }
+    }
+    std::vector<int2> outline;
+    std::vector<float4> pts;
+    build_face_outlines(verts, tris, tri_face, nt, nf, planes.data(), outline, pts);
+    for (int f = 0; f < nf; ++f) corners[f] = outline[f].y;
+    return SBR_OK;
+}
+
 sbr_status sbr_scene_wedges(const sbr_scene *scene, float *ab, int32_t *faces, int64_t cap, int64_t *count) {
     if (!scene || !count || cap < 0 || (cap > 0 && (!ab || !faces))) return SBR_EINVAL;
     *count = (int64_t)scene->wedges.size();

@@ -76,3 +76,60 @@ def test_oracle_not_imported_by_product():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "sbr_oracle" not in txt, f
+
+
+def _outline_corners(lib, sc):
+    import ctypes
+    V = np.ascontiguousarray(np.asarray(sc.verts, np.float32))
+    T = np.ascontiguousarray(np.asarray(sc.tris, np.int32))
+    F = np.ascontiguousarray(np.asarray(sc.tri_face, np.int32))
+    nf = int(F.max()) + 1
+    out = np.full(nf, -1, np.int32)
+    pf, pi = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)
+    st = lib.sbr_face_outline_corners(V.ctypes.data_as(pf), len(V), T.ctypes.data_as(pi), F.ctypes.data_as(pi),
+                                      len(T), nf, out.ctypes.data_as(pi))
+    assert st == 0
+    return out
+
+
+def test_face_outline_corners(lib):
+    """Host logic of the validity test's point-in-face query (§III.A): a face is tested
+    against its convex outline exactly when its triangles tile a convex polygon.  Tiled
+    rectangles, a triangle and a convex hexagon qualify with their corner counts; an
+    L-shape, a ring around a hole, a bent face, a doubled quad and a flipped triangle keep
+    the triangle-by-triangle query."""
+    from paper_2208_10009_gb300 import scenes
+    b = scenes._Builder()
+    scenes.box_faces(b, (0, 0, 0), (2, 3, 4), 3)                     # faces 0-5: 3 x 3 tiled rectangles
+    tri = b.polygon([(5, 0, 0), (6, 0, 0), (5, 1, 0.5)])
+    ang = np.linspace(0, 2 * np.pi, 7)[:-1]
+    hexa = b.polygon(np.c_[10 + np.cos(ang), np.sin(ang), np.zeros(6)])
+    ell = b.nf
+    b.nf += 1
+    for (y0, y1, z0, z1) in ((0, 3, 0, 1.5), (3, 6, 0, 1.5), (0, 3, 1.5, 3)):
+        b.quad((20, y0, z0), (20, y1, z0), (20, y0, z1), face=ell)
+    ring = b.nf
+    b.nf += 1
+    for i in range(3):
+        for j in range(3):
+            if (i, j) != (1, 1):
+                b.quad((30 + i, j, 0), (31 + i, j, 0), (30 + i, j + 1, 0), face=ring)
+    bent = b.nf
+    b.nf += 1
+    b.polygon([(40, 0, 0), (41, 0, 0), (41, 1, 0)], face=bent)
+    b.polygon([(40, 0, 0), (41, 1, 0), (40, 1, 0.3)], face=bent)
+    dup = b.nf
+    b.nf += 1
+    b.quad((50, 0, 0), (51, 0, 0), (50, 1, 0), face=dup)
+    b.quad((50, 0, 0), (51, 0, 0), (50, 1, 0), face=dup)
+    flip = b.nf
+    b.nf += 1
+    b.polygon([(60, 0, 0), (61, 0, 0), (61, 1, 0)], face=flip)
+    b.polygon([(60, 0, 0), (60, 1, 0), (61, 1, 0)], face=flip)        # wound against the first
+    sc = b.finish()
+    c = _outline_corners(lib, sc)
+    nbox = tri
+    assert np.all(c[:nbox] == 4), c[:nbox]
+    assert c[tri] == 3 and c[hexa] == 6
+    for f in (ell, ring, bent, dup, flip):
+        assert c[f] == 0, (f, c[f])
