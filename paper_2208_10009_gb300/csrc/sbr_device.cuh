@@ -74,27 +74,6 @@ __device__ __forceinline__ RayPre make_ray(float3 o, float3 d) {
     return r;
 }
 
-// Slab test of both children of a BVH node; returns a 2-bit hit mask and entry distances.
-// The far bound is widened by a few ulps so that rounding never culls a box the ray
-// actually touches (zero-thickness boxes of axis-aligned walls included).
-__device__ __forceinline__ int slab2(const float4 *node, const RayPre &r, float tmin, float tmax, float &t0,
-                                     float &t1) {
-    float4 a = __ldg(node + 0), b = __ldg(node + 1), c = __ldg(node + 2);
-    float lx0 = (a.x - r.o.x) * r.inv.x, hx0 = (a.w - r.o.x) * r.inv.x;
-    float ly0 = (a.y - r.o.y) * r.inv.y, hy0 = (b.x - r.o.y) * r.inv.y;
-    float lz0 = (a.z - r.o.z) * r.inv.z, hz0 = (b.y - r.o.z) * r.inv.z;
-    float lx1 = (b.z - r.o.x) * r.inv.x, hx1 = (c.y - r.o.x) * r.inv.x;
-    float ly1 = (b.w - r.o.y) * r.inv.y, hy1 = (c.z - r.o.y) * r.inv.y;
-    float lz1 = (c.x - r.o.z) * r.inv.z, hz1 = (c.w - r.o.z) * r.inv.z;
-    float n0 = fmaxf(fmaxf(fminf(lx0, hx0), fminf(ly0, hy0)), fmaxf(fminf(lz0, hz0), tmin));
-    float f0 = fminf(fminf(fmaxf(lx0, hx0), fmaxf(ly0, hy0)), fminf(fmaxf(lz0, hz0), tmax)) * 1.0000005f;
-    float n1 = fmaxf(fmaxf(fminf(lx1, hx1), fminf(ly1, hy1)), fmaxf(fminf(lz1, hz1), tmin));
-    float f1 = fminf(fminf(fmaxf(lx1, hx1), fmaxf(ly1, hy1)), fminf(fmaxf(lz1, hz1), tmax)) * 1.0000005f;
-    t0 = n0;
-    t1 = n1;
-    return (n0 <= f0 ? 1 : 0) | (n1 <= f1 ? 2 : 0);
-}
-
 // Three-input min / max (one instruction each on sm_100 and later).
 __device__ __forceinline__ float max3f(float a, float b, float c) {
     float d;
@@ -131,62 +110,6 @@ __device__ __forceinline__ float tri_watertight(const RayPre &r, float4 A4, floa
     return T / det;
 }
 
-// Closest hit along o + t d over t in (tmin, tmax], skipping triangles of face `skip`.
-// Ties in t go to the lower face id, then the lower triangle index.  Returns the
-// triangle index (BVH order) or -1; t_out, face_out set on a hit.
-__device__ __forceinline__ int closest_hit(const SceneDev &S, const RayPre &r, float tmin, float tmax, int skip,
-                                           float &t_out, int &face_out, unsigned &nodes_visited,
-                                           unsigned &tris_tested) {
-    int stack[kStackDepth];
-    int sp = 0;
-    int node = 0;
-    float tbest = tmax;
-    int best = -1, bface = 0x7fffffff;
-    for (;;) {
-        if (!is_leaf(node)) {
-            ++nodes_visited;
-            const float4 *nd = S.nodes + 4 * (size_t)node;
-            float e0, e1;
-            int m = slab2(nd, r, tmin, tbest, e0, e1);
-            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 3));
-            if (m == 3) {
-                int nearc = e0 <= e1 ? refs.x : refs.y;
-                int farc = e0 <= e1 ? refs.y : refs.x;
-                stack[sp++] = farc;
-                node = nearc;
-                continue;
-            } else if (m == 1) {
-                node = refs.x;
-                continue;
-            } else if (m == 2) {
-                node = refs.y;
-                continue;
-            }
-        } else {
-            int first = leaf_first(node), cnt = leaf_count(node);
-            for (int i = first; i < first + cnt; ++i) {
-                const float4 *t = S.tris + 3 * (size_t)i;
-                float4 a = __ldg(t), b = __ldg(t + 1), c = __ldg(t + 2);
-                int f = __float_as_int(a.w);
-                if (f == skip) continue;
-                ++tris_tested;
-                float th = tri_watertight(r, a, b, c);
-                if (!(th > tmin) || th > tbest) continue;
-                if (th < tbest || f < bface || (f == bface && i < best)) {
-                    tbest = th;
-                    best = i;
-                    bface = f;
-                }
-            }
-        }
-        if (sp == 0) break;
-        node = stack[--sp];
-    }
-    t_out = tbest;
-    face_out = bface;
-    return best;
-}
-
 // Two FMAs in one packed f32x2 instruction: (a.x * b + c, a.y * b + c).
 __device__ __forceinline__ float2 fma2s(float ax, float ay, float b, float c) {
     float2 r;
@@ -219,8 +142,10 @@ __device__ __forceinline__ void cswap(float &da, int &ra, float &db, int &rb) {
 // t = plane * (1/d) - o * (1/d), the near / far planes picked by the ray's direction
 // signs (so no per-axis min/max), two children per packed FMA and three-input min/max;
 // the hit children are sorted by entry distance, the nearest is visited next and the
-// others pushed farthest first.  Same hit rule as closest_hit.  nodes_visited counts
-// 4-wide nodes (four box tests each).
+// others pushed farthest first.  Closest hit along o + t d over t in (tmin, tmax],
+// skipping triangles of face `skip`; ties in t go to the lower face id, then the lower
+// triangle index.  Returns the triangle index (BVH order) or -1; t_out, face_out set on a
+// hit.  nodes_visited counts 4-wide nodes (four box tests each).
 __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, float tmin, float tmax, int skip,
                                             float &t_out, int &face_out, unsigned &nodes_visited,
                                             unsigned &tris_tested) {
@@ -301,49 +226,8 @@ __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, 
     return best;
 }
 
-// Any hit of the segment o + t d, t in (tmin, tmax), ignoring faces fa and fb.
-__device__ __forceinline__ bool any_hit(const SceneDev &S, const RayPre &r, float tmin, float tmax, int fa, int fb) {
-    int stack[kStackDepth];
-    int sp = 0;
-    int node = 0;
-    for (;;) {
-        if (!is_leaf(node)) {
-            const float4 *nd = S.nodes + 4 * (size_t)node;
-            float e0, e1;
-            int m = slab2(nd, r, tmin, tmax, e0, e1);
-            int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 3));
-            if (m == 3) {
-                stack[sp++] = refs.y;
-                node = refs.x;
-                continue;
-            } else if (m == 1) {
-                node = refs.x;
-                continue;
-            } else if (m == 2) {
-                node = refs.y;
-                continue;
-            }
-        } else {
-            int first = leaf_first(node), cnt = leaf_count(node);
-            for (int i = first; i < first + cnt; ++i) {
-                const float4 *t = S.tris + 3 * (size_t)i;
-                float4 a = __ldg(t), b = __ldg(t + 1), c = __ldg(t + 2);
-                int f = __float_as_int(a.w);
-                if (f == fa || f == fb) continue;
-                float th = tri_watertight(r, a, b, c);
-                if (th > tmin && th < tmax) return true;
-            }
-        }
-        if (sp == 0) break;
-        node = stack[--sp];
-    }
-    return false;
-}
-
 // Any hit of the segment o + t d, t in (tmin, tmax), ignoring faces fa and fb, over the
-// 4-wide BVH (the same triangles and the same triangle test as any_hit, so the same
-// answer, with fewer node visits); inner nodes and leaves in nested loops as in
-// closest_hit4.
+// 4-wide BVH; inner nodes and leaves in nested loops as in closest_hit4.
 __device__ __forceinline__ bool any_hit4(const SceneDev &S, const RayPre &r, float tmin, float tmax, int fa, int fb) {
     int stack[kStack4];
     int sp = 0;
