@@ -7,11 +7,12 @@ arithmetic lives in ``sbr_oracle.c`` (plain C, double precision, brute force), a
 module only marshals arrays and groups records.  The one module both sides use is the
 seeded scene generator, which holds none of the method's arithmetic.
 
-Parity status: every function is pinned by the tests under ``tests/`` except the power
-term of :func:`path_eval`, whose formula the paper does not give (parity unpinned
-beyond the single-plane closed form), and the power term of :func:`wedge_eval` /
-:func:`wedge_image` (free-space loss only: the paper gives no diffraction coefficient;
-parity unpinned).
+Parity status: every function is pinned by the tests under ``tests/``.  Two power terms
+rest on readings because the paper gives no formula: the reflection power of
+:func:`path_eval` (pinned only by single-plane closed forms: free-space loss, the
+normal-incidence Fresnel coefficient, the grazing limit) and the diffraction power of
+:func:`wedge_eval` / :func:`wedge_image` (free-space loss only, no diffraction
+coefficient; pinned by the unrolled-edge closed form around a single wedge).
 """
 from __future__ import annotations
 
@@ -78,6 +79,9 @@ def _load():
                                            _d, _d, _i64]),
             "ora_refine": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, _d, ctypes.c_double, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, _d, _d, _i32, _d]),
+            "ora_refine_ex": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, _d, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_double, _i32, ctypes.c_int, _d, _d, _i32, _d,
+                                             _d]),
             "ora_path_eval": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, _d, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, _d, _i32, _d, _d, _d, _d, _d]),
             "ora_image_path": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, ctypes.c_double,
@@ -310,6 +314,33 @@ def refine(scene: Scene, tx, rx, faces, c0, R0: float, K: int, iters: int, targe
     if it < 0:
         raise ValueError("bad sub-ray count")
     return dict(dir=out_dir, err=float(out_err[0]), iters=it, choice=choice[:it], err_hist=hist[: it + 1])
+
+
+def refine_ex(scene: Scene, tx, rx, faces, c0, R0: float, K: int, iters: int, target: float = 0.0, forced=None,
+              stall: bool = True):
+    """``refine`` with the test hooks of ``ora_refine_ex``: ``forced`` (a sequence of
+    sub-ray indices, -1 = argmin) replays another implementation's choices; the result
+    adds ``sub_err`` (iterations x K: every sub-ray's error angle per iteration).
+    ``stall=False`` disables the stalled-path exit."""
+    fa = _faces_arr(faces)
+    out_dir = np.zeros(3)
+    out_err = np.zeros(1)
+    n = max(iters, 1)
+    choice = np.full(n, -1, np.int32)
+    hist = np.full(iters + 1, np.nan)
+    sub = np.full((n, K), np.nan)
+    fz = None
+    if forced is not None:
+        fz = np.full(n, -1, np.int32)
+        f = np.asarray(forced, np.int32)[:n]
+        fz[: len(f)] = f
+    it = _load().ora_refine_ex(scene.handle, _p(_f64(tx, (3,))), _p(_f64(rx, (3,))), len(faces), _p(fa, _i32),
+                               _p(_f64(c0, (3,))), R0, K, iters, target, _p(fz, _i32), int(stall), _p(out_dir),
+                               _p(out_err), _p(choice, _i32), _p(hist), _p(sub))
+    if it < 0:
+        raise ValueError("bad sub-ray count")
+    return dict(dir=out_dir, err=float(out_err[0]), iters=it, choice=choice[:it], err_hist=hist[: it + 1],
+                sub_err=sub[:it])
 
 
 def refined_err_bound(R0: float, K: int, iters: int) -> float:

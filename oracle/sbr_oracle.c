@@ -757,9 +757,10 @@ static void cone_frame(vec3 c, vec3 *u, vec3 *v) {
  * follows, and since 1 / (1 - s) + 2 s >= 2 for every pattern it is rejected now as well.
  * Valid paths never meet this condition, so their results are unchanged.
  */
-int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
-               const double *c0, double R0, int K, int iters, double target,
-               double *out_dir, double *out_err, int32_t *choice, double *err_hist) {
+static int refine_core(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
+                       const double *c0, double R0, int K, int iters, double target, const int32_t *forced,
+                       int stall_on, double *out_dir, double *out_err, int32_t *choice, double *err_hist,
+                       double *sub_err) {
     const scene *s = (const scene *)sp;
     double rho[16], phi[16], shrink;
     if (ora_subray_pattern(K, rho, phi, &shrink) != K) return -1;
@@ -772,7 +773,8 @@ int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const 
     if (err_hist) err_hist[0] = err;
     int it = 0;
     const double stall = 1.0 / (1.0 - shrink) + 2.0 * shrink;
-    while (it < iters && !(target > 0 && err <= target && aoa <= target) && !(err > R * stall + 1e-6)) {
+    while (it < iters && !(target > 0 && err <= target && aoa <= target) &&
+           !(stall_on && err > R * stall + 1e-6)) {
         vec3 u, v, best_d = c;
         double best = INFINITY;
         int bk = -1;
@@ -781,9 +783,14 @@ int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const 
             double a = rho[k] * R;
             vec3 dk = add(scl(c, cos(a)), scl(add(scl(u, cos(phi[k])), scl(v, sin(phi[k]))), sin(a)));
             double e = trace_planes(s, tx, rx, order, faces, dk, NULL, NULL);
-            if (e < best) { best = e; bk = k; best_d = dk; }
+            if (sub_err) sub_err[(size_t)it * K + k] = e;
+            if (forced && forced[it] >= 0) {
+                if (k == forced[it]) { best = e; bk = k; best_d = dk; }
+            } else if (e < best) {
+                best = e; bk = k; best_d = dk;
+            }
         }
-        if (bk < 0) break;
+        if (bk < 0 || !(best < INFINITY)) break;
         c = best_d;
         err = best;
         if (target > 0) aoa = aoa_error(s, tx, rx, order, faces, c, txk);
@@ -795,6 +802,30 @@ int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const 
     st(out_dir, c);
     *out_err = err;
     return it;
+}
+
+int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
+               const double *c0, double R0, int K, int iters, double target,
+               double *out_dir, double *out_err, int32_t *choice, double *err_hist) {
+    return refine_core(sp, tx3, rx3, order, faces, c0, R0, K, iters, target, NULL, 1, out_dir, out_err, choice,
+                       err_hist, NULL);
+}
+
+/*
+ * The same iteration with two test hooks that leave its arithmetic unchanged: sub_err
+ * (iters x K, or NULL) receives every sub-ray's error angle per iteration, and forced (or
+ * NULL) names the sub-ray each iteration keeps instead of the argmin (a negative entry
+ * keeps the argmin).  Replaying another implementation's choice sequence this way gives
+ * the exact FP64 state that implementation approximates, so each of its choices can be
+ * compared with the best sub-ray of the same cone.  stall_on = 0 disables the stalled-
+ * path exit (everything else as ora_refine).
+ */
+int ora_refine_ex(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
+                  const double *c0, double R0, int K, int iters, double target, const int32_t *forced,
+                  int stall_on, double *out_dir, double *out_err, int32_t *choice, double *err_hist,
+                  double *sub_err) {
+    return refine_core(sp, tx3, rx3, order, faces, c0, R0, K, iters, target, forced, stall_on, out_dir, out_err,
+                       choice, err_hist, sub_err);
 }
 
 /* point-in-face: p lies inside (or on the boundary of) some triangle of face f */

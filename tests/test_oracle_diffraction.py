@@ -238,3 +238,38 @@ def test_pipeline_diffraction_in_canyon_block(oracle_mod):
     exact = {(r, w) for r in range(len(rx)) for w in oracle_mod.wedge_enumerate(S, tx[0], rx[r])}
     assert len(exact) > 5
     assert found == exact
+
+
+def test_diffraction_power_closed_form(oracle_mod):
+    """Power of an order-1 diffraction path (§IV outputs; the paper gives no diffraction
+    coefficient, so the power term is free-space loss over the path length).  Around the
+    vertical edge x = y = 0 of a box, a path from Tx to Rx unrolls about the edge into a
+    straight line: with rho_t, rho_r the two points' distances from the edge line and dz
+    their height difference, the length is hypot(rho_t + rho_r, dz), the diffraction point
+    sits at height z_t + dz rho_t / (rho_t + rho_r), and the power at 2.4 GHz is
+    P_tx + 20 log10(lambda / (4 pi L)).  Checked on exact paths and on refined launch
+    directions (wedge_eval) for several transmit powers and frequencies."""
+    S = oracle_mod.Scene.from_generated(_box((0, 0, 0), (2, 3, 4), bottom=False))
+    ab, fc = oracle_mod.wedges(S)
+    w = [i for i in range(len(fc)) if np.allclose(ab[i, :, :2], 0)][0]
+    cases = [([-5.0, 1.5, 1.0], [1.5, -4.0, 1.2]), ([-3.0, 2.0, 3.5], [2.5, -6.0, 0.5]),
+             ([-1.0, 0.2, 2.0], [0.7, -9.0, 3.9])]
+    for (tx, rx), (freq, ptx) in zip(cases, [(2.4e9, 0.0), (5.8e9, 20.0), (28e9, -3.0)]):
+        tx, rx = np.array(tx), np.array(rx)
+        rt, rr = np.hypot(tx[0], tx[1]), np.hypot(rx[0], rx[1])
+        L = np.hypot(rt + rr, rx[2] - tx[2])
+        zq = tx[2] + (rx[2] - tx[2]) * rt / (rt + rr)
+        want = ptx + 20 * np.log10(C0 / freq / (4 * np.pi * L))
+        im = oracle_mod.wedge_image(S, tx, rx, w, freq=freq, ptx_dbm=ptx)
+        assert im["valid"]
+        assert np.allclose(im["point"], [0, 0, zq], atol=1e-12)
+        assert abs(im["delay"] * C0 - L) < 1e-12 * L
+        assert abs(im["power"] - want) < 1e-10
+        ev = oracle_mod.wedge_eval(S, tx, rx, w, im["aod_dir"], freq=freq, ptx_dbm=ptx)
+        assert ev["valid"] and abs(ev["power"] - want) < 1e-9
+        # a launch direction off the exact one by 1e-4 rad: length and power move by the
+        # second-order amount (the exact path is stationary)
+        d = im["aod_dir"] + np.array([0.0, 0.0, 1e-4])
+        ev = oracle_mod.wedge_eval(S, tx, rx, w, d / np.linalg.norm(d), freq=freq, ptx_dbm=ptx)
+        assert 0 <= ev["delay"] * C0 - L < 1e-6 * L
+        assert abs(ev["power"] - want) < 1e-5
