@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define SBR_ABI_VERSION 2
+#define SBR_ABI_VERSION 3
 #define SBR_MAX_ORDER 8
 
 typedef enum {
@@ -46,7 +46,8 @@ typedef enum {
     SBR_ETIMEOUT = 4,    /* a bounded device-side wait gave up (persistent queue) */
     SBR_EOVERFLOW = 5,   /* a record or path buffer was too small; counts say how large */
     SBR_EDEGENERATE = 6, /* scene has NaN/Inf vertices, zero-area triangles or bad ids */
-    SBR_ECOLLISION = 7   /* two different face sequences shared a 64-bit dedup hash */
+    SBR_ECOLLISION = 7,  /* two different face sequences shared a 64-bit dedup hash */
+    SBR_ECHECK = 8       /* SBR_CHECKED builds: a device bounds check failed (see check_flags) */
 } sbr_status;
 
 typedef struct sbr_ctx sbr_ctx;
@@ -179,6 +180,9 @@ typedef struct {
                                 (1..32; 0 = 16: keeps a warp's rays neighbours in the lattice) */
     int32_t launcher;        /* 0 = equiangular (§II.B), 20 / 8 = equidistant icosahedron /
                                 octahedron (§II.A); ray ids follow that launcher's order */
+    int64_t ray_begin;       /* with SBR_LAUNCH_RAY_RANGE: trace only ray ids [ray_begin, ray_end) */
+    int64_t ray_end;         /* of every transmitter (0 <= ray_begin <= ray_end <= N; rays are
+                                independent, §III.A, so disjoint ranges split one launch) */
 } sbr_launch_params;
 
 #define SBR_LAUNCH_SYNC 1    /* synchronise at the end and report overflow / collisions */
@@ -191,6 +195,10 @@ typedef struct {
                                     into the half-plane opposite Tx) is within the cone and
                                     whose segment from the edge is unblocked gets a record;
                                     the path has order 1 and faces[0] = -1 - wedge id */
+#define SBR_LAUNCH_RAY_RANGE 8  /* trace only ray_begin..ray_end of each transmitter; record ray
+                                   ids stay the lattice's own (position-independent records) */
+#define SBR_LAUNCH_RECORDS_ONLY 16 /* stop after the reception judgment: the container keeps the
+                                      reception records (sbr_records_read) and no paths */
 
 typedef struct {
     int64_t rays;            /* rays traced (ntx * N) */
@@ -209,6 +217,9 @@ typedef struct {
     int64_t diffraction_records;         /* diffraction records emitted */
     int64_t diffraction_candidates;      /* (ray, wedge) candidates (may exceed candidate_cap) */
     int64_t candidate_cap;               /* candidates the container holds: 1.25 x record_cap or more */
+    int64_t check_flags;                 /* SBR_CHECK_* bits of failed device bounds checks of the
+                                            container's work since its last launch (SBR_CHECKED
+                                            builds; always 0 otherwise) */
 } sbr_launch_stats;
 
 /* a1-a5 -- §III.A / Fig. 4: launch N rays from each of ntx transmitters (tx: ntx x 3
@@ -221,8 +232,52 @@ typedef struct {
  * sbr_launch_get_stats (and by the SYNC return code). */
 sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int32_t ntx,
                       const sbr_rxset *rx, const sbr_launch_params *params, sbr_paths *paths);
+/* Bounds checks of SBR_CHECKED builds (the library compiled with -DSBR_CHECKED; the
+ * environment variable SBR_CHECKED_STACK_LIMIT, read at scene upload, lowers the traversal
+ * stack entries a walk may use, to exercise the checks).  A failed check sets its bit in the
+ * container's status word and stops the query that failed (a miss, or an unoccluded
+ * segment): no assert, no trap.  sbr_launch with SBR_LAUNCH_SYNC and sbr_query then return
+ * SBR_ECHECK, naming the failed checks in sbr_last_error. */
+#define SBR_CHECK_TRACE_STACK 1      /* closest-hit walk of the trace */
+#define SBR_CHECK_OCCLUSION_STACK 2  /* any-hit walk of the validity test */
+#define SBR_CHECK_RX_STACK 4         /* receiver walk of the reception judgment */
+#define SBR_CHECK_FACE_ID 8          /* a face id outside [0, num_faces) met on the device */
+#define SBR_CHECK_BVH2_STACK 16      /* binary-BVH walks (point in face, wedge search) */
+
 /* Synchronises the stream and reads the counters of the container's last launch. */
 sbr_status sbr_launch_get_stats(sbr_ctx *ctx, const sbr_paths *paths, sbr_launch_stats *out);
+
+/* ---------------------------------------------------------------- reception records */
+/* One reception record of §III.A (Fig. 4): ray `ray` of transmitter `tx`, on the segment
+ * after `order` reflections on faces[0..order), received Rx `rx` inside its cone with the
+ * error angle of Eq. 3 and propagation distance dray to the foot of Rx.  Order-1
+ * diffraction records have faces[0] = -1 - wedge id.  Records name lattice ray ids and hold
+ * no buffer positions, so records of disjoint ray ranges can be concatenated. */
+typedef struct {
+    int32_t tx, rx, ray, order;
+    int32_t faces[SBR_MAX_ORDER]; /* -1 padded */
+    float err;               /* Eq. 3 error angle (rad) */
+    float dray;              /* distance along the ray to the foot of Rx (m) */
+    int32_t slot;            /* library-internal (dedup table slot); ignored on input */
+    int32_t pad;
+} sbr_reception_record;      /* 64 bytes */
+
+/* Copy up to cap of the reception records the container's last sbr_launch emitted (before
+ * double-count removal; order unspecified) to `out` (host or device); *written = records
+ * copied.  The launch's total is sbr_launch_stats.records (records beyond record_cap were
+ * dropped and are not copied).  Synchronises. */
+sbr_status sbr_records_read(sbr_ctx *ctx, const sbr_paths *paths, sbr_reception_record *out, int64_t cap,
+                            int64_t *written);
+/* a5 -- §III.A, first path test, on a given record set: replace the container's records
+ * with `count` records from `in` (host or device, e.g. the concatenated records of launches
+ * over disjoint ray ranges) and remove double counts exactly as sbr_launch does (per (Tx,
+ * Rx, face sequence) the smallest error angle, ties to the lowest ray id).  The paths that
+ * replace the container's are those whose pair is owned by shard `rank` of `world`:
+ * (tx * nrx + rx) mod world == rank (world = 1: all).  The container must hold a launch of
+ * the same transmitters, receivers and division level (its refinement context is kept).
+ * SBR_EOVERFLOW if count > record_cap; SBR_EINVAL unless 0 <= rank < world.  Asynchronous. */
+sbr_status sbr_records_dedup(sbr_ctx *ctx, sbr_paths *paths, const sbr_reception_record *in, int64_t count,
+                             int32_t rank, int32_t world);
 
 /* ---------------------------------------------------------------- refinement */
 typedef struct {
@@ -234,7 +289,9 @@ typedef struct {
                                 this (default 1e-5 when 0) */
     double freq_hz;          /* carrier for the power term (0: 2.4e9) */
     double ptx_dbm;          /* transmit power */
-    int8_t *choice_log;      /* device [path_cap][max_iters] argmin sub-ray per iteration, or NULL */
+    int8_t *choice_log;      /* device [path_cap][max_iters], or NULL: per iteration the argmin
+                                sub-ray k (bits 0-3) and the sub-cone frame's reference axis
+                                0/1/2 = x/y/z (bits 4-5: the world axis of smallest |c_i|) */
 } sbr_refine_params;
 
 /* a6-a8 -- §III.B, Fig. 5, Eq. 10 and §III.A: refine every path of the container.  The
@@ -247,7 +304,9 @@ typedef struct {
  * (bounce points inside their faces, no segment occluded) and the outputs (delay, AOD,
  * AOA, power).  One thread per path, static schedule. */
 sbr_status sbr_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths, const sbr_refine_params *params);
-/* Same as sbr_refine restricted to the paths of one (tx, rx) pair: the per-pair form. */
+/* Same as sbr_refine restricted to the paths of one (tx, rx) pair: the per-pair form.  The
+ * first call after a launch groups the paths by pair and reads the groups' ranges back to
+ * the host once (synchronises); later calls are asynchronous. */
 sbr_status sbr_refine_pair(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths, int32_t tx, int32_t rx,
                            const sbr_refine_params *params);
 
@@ -300,6 +359,10 @@ typedef struct {
                                  test asks the diffraction point to lie on the wedge, both
                                  ends in its exterior and both legs unblocked; power is free-
                                  space loss only (the paper gives no diffraction coefficient) */
+
+/* Number of the container's valid paths with a non-finite output (direction, error angle,
+ * delay, AOD, AOA or power): a device scan, 0 when the outputs are sound.  Synchronises. */
+sbr_status sbr_paths_nonfinite(sbr_ctx *ctx, const sbr_paths *paths, int64_t *count);
 
 /* Number of paths in the container (synchronises). */
 sbr_status sbr_paths_count(sbr_ctx *ctx, const sbr_paths *paths, int64_t *out);

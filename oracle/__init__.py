@@ -81,7 +81,7 @@ def _load():
                                           ctypes.c_int, ctypes.c_double, _d, _d, _i32, _d]),
             "ora_refine_ex": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, _d, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_double, _i32, ctypes.c_int, _d, _d, _i32, _d,
-                                             _d]),
+                                             _d, _i32, _d]),
             "ora_path_eval": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, _d, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, _d, _i32, _d, _d, _d, _d, _d]),
             "ora_image_path": (ctypes.c_int, [_vp, _d, _d, ctypes.c_int, _i32, ctypes.c_double,
@@ -90,6 +90,8 @@ def _load():
                                                      _d, _d]),
             "ora_unfold": (None, [_vp, ctypes.c_int, _i32, _d, _d, ctypes.c_double, ctypes.c_double, _d, _d]),
             "ora_num_threads": (ctypes.c_int, []),
+            "ora_unfold_many": (None, [_vp, ctypes.c_int64, _i32, _i32, _d, _d, _d]),
+            "ora_path_errors": (None, [_vp, _d, _d, ctypes.c_int, _i32, _d, _d]),
             "ora_equidistant": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, _d]),
             "ora_wedges": (ctypes.c_int32, [_vp, _d, _i32]),
             "ora_wedge_exterior": (ctypes.c_int32, [_vp, ctypes.c_int32, _d]),
@@ -318,10 +320,12 @@ def refine(scene: Scene, tx, rx, faces, c0, R0: float, K: int, iters: int, targe
 
 def refine_ex(scene: Scene, tx, rx, faces, c0, R0: float, K: int, iters: int, target: float = 0.0, forced=None,
               stall: bool = True):
-    """``refine`` with the test hooks of ``ora_refine_ex``: ``forced`` (a sequence of
-    sub-ray indices, -1 = argmin) replays another implementation's choices; the result
-    adds ``sub_err`` (iterations x K: every sub-ray's error angle per iteration).
-    ``stall=False`` disables the stalled-path exit."""
+    """``refine`` with the test hooks of ``ora_refine_ex``: ``forced`` (per iteration the
+    sub-ray index in bits 0-3 and the frame axis in bits 4-5, or -1 for the argmin and the
+    frame rule) replays another implementation's logged choices; the result adds
+    ``sub_err`` (iterations x K: every sub-ray's error angle per iteration), ``axis`` (the
+    frame axis the rule picks at each iteration's centre) and ``centre`` (each iteration's
+    cone centre).  ``stall=False`` disables the stalled-path exit."""
     fa = _faces_arr(faces)
     out_dir = np.zeros(3)
     out_err = np.zeros(1)
@@ -334,13 +338,25 @@ def refine_ex(scene: Scene, tx, rx, faces, c0, R0: float, K: int, iters: int, ta
         fz = np.full(n, -1, np.int32)
         f = np.asarray(forced, np.int32)[:n]
         fz[: len(f)] = f
+    axis = np.full(n, -1, np.int32)
+    centre = np.full((n, 3), np.nan)
     it = _load().ora_refine_ex(scene.handle, _p(_f64(tx, (3,))), _p(_f64(rx, (3,))), len(faces), _p(fa, _i32),
                                _p(_f64(c0, (3,))), R0, K, iters, target, _p(fz, _i32), int(stall), _p(out_dir),
-                               _p(out_err), _p(choice, _i32), _p(hist), _p(sub))
+                               _p(out_err), _p(choice, _i32), _p(hist), _p(sub), _p(axis, _i32), _p(centre))
     if it < 0:
         raise ValueError("bad sub-ray count")
     return dict(dir=out_dir, err=float(out_err[0]), iters=it, choice=choice[:it], err_hist=hist[: it + 1],
-                sub_err=sub[:it])
+                sub_err=sub[:it], axis=axis[:it], centre=centre[:it])
+
+
+def path_errors(scene: Scene, tx, rx, faces, direction):
+    """(AOD error, AOA error) of a reflection path launched along ``direction``: the two
+    quantities the precise algorithm's early stop compares with its target."""
+    fa = _faces_arr(faces)
+    out = np.zeros(2)
+    _load().ora_path_errors(scene.handle, _p(_f64(tx, (3,))), _p(_f64(rx, (3,))), len(faces), _p(fa, _i32),
+                            _p(_f64(direction, (3,))), _p(out))
+    return float(out[0]), float(out[1])
 
 
 def refined_err_bound(R0: float, K: int, iters: int) -> float:
@@ -401,6 +417,17 @@ def unfold(scene: Scene, faces, tx, rx, az: float, el: float):
     _load().ora_unfold(scene.handle, len(faces), _p(fa, _i32), _p(_f64(tx, (3,))), _p(_f64(rx, (3,))),
                        float(az), float(el), _p(val), _p(J))
     return val, J
+
+
+def unfold_many(scene: Scene, order, faces, tx, rx) -> np.ndarray:
+    """``unfold`` values (miss[3] at az = el = 0, delay, AOD az/el, AOA az/el) of many
+    reflection paths: order (P,), faces (P, 8) -1 padded, tx / rx (P, 3)."""
+    order = np.ascontiguousarray(np.asarray(order, np.int32))
+    faces = np.ascontiguousarray(np.asarray(faces, np.int32).reshape(-1, MAX_ORDER))
+    tx, rx = _f64(tx, (-1, 3)), _f64(rx, (-1, 3))
+    out = np.zeros((len(order), 8))
+    _load().ora_unfold_many(scene.handle, len(order), _p(order, _i32), _p(faces, _i32), _p(tx), _p(rx), _p(out))
+    return out
 
 
 def az_el(v):

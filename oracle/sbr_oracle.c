@@ -724,14 +724,20 @@ static double aoa_error(const scene *s, vec3 tx, vec3 rx, int order, const int32
  * Sub-cone frame for cone centre c: u = normalize(c x e), e the world axis with the
  * smallest |c . e_i| (lowest index on ties); v = c x u.
  */
-static void cone_frame(vec3 c, vec3 *u, vec3 *v) {
+static int frame_axis(vec3 c) {
     double ax = fabs(c.x), ay = fabs(c.y), az = fabs(c.z);
-    vec3 e = mk(1, 0, 0);
-    if (ay < ax && ay <= az) e = mk(0, 1, 0);
-    else if (az < ax && az < ay) e = mk(0, 0, 1);
+    if (ay < ax && ay <= az) return 1;
+    if (az < ax && az < ay) return 2;
+    return 0;
+}
+
+static void frame_on_axis(vec3 c, int a, vec3 *u, vec3 *v) {
+    vec3 e = mk(a == 0, a == 1, a == 2);
     *u = unit(cross(c, e));
     *v = cross(c, *u);
 }
+
+static void cone_frame(vec3 c, vec3 *u, vec3 *v) { frame_on_axis(c, frame_axis(c), u, v); }
 
 /*
  * The iterative precise algorithm (§III.B, Fig. 5, Eq. 10).  The path's initial cone
@@ -760,7 +766,7 @@ static void cone_frame(vec3 c, vec3 *u, vec3 *v) {
 static int refine_core(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
                        const double *c0, double R0, int K, int iters, double target, const int32_t *forced,
                        int stall_on, double *out_dir, double *out_err, int32_t *choice, double *err_hist,
-                       double *sub_err) {
+                       double *sub_err, int32_t *axis_log, double *centre_log) {
     const scene *s = (const scene *)sp;
     double rho[16], phi[16], shrink;
     if (ora_subray_pattern(K, rho, phi, &shrink) != K) return -1;
@@ -778,14 +784,17 @@ static int refine_core(void *sp, const double *tx3, const double *rx3, int order
         vec3 u, v, best_d = c;
         double best = INFINITY;
         int bk = -1;
-        cone_frame(c, &u, &v);
+        const int fz = forced ? forced[it] : -1;
+        if (axis_log) axis_log[it] = frame_axis(c);
+        if (centre_log) st(centre_log + 3 * (size_t)it, c);
+        frame_on_axis(c, fz >= 0 ? (fz >> 4) & 3 : frame_axis(c), &u, &v);
         for (int k = 0; k < K; ++k) {
             double a = rho[k] * R;
             vec3 dk = add(scl(c, cos(a)), scl(add(scl(u, cos(phi[k])), scl(v, sin(phi[k]))), sin(a)));
             double e = trace_planes(s, tx, rx, order, faces, dk, NULL, NULL);
             if (sub_err) sub_err[(size_t)it * K + k] = e;
-            if (forced && forced[it] >= 0) {
-                if (k == forced[it]) { best = e; bk = k; best_d = dk; }
+            if (fz >= 0) {
+                if (k == (fz & 15)) { best = e; bk = k; best_d = dk; }
             } else if (e < best) {
                 best = e; bk = k; best_d = dk;
             }
@@ -808,24 +817,41 @@ int ora_refine(void *sp, const double *tx3, const double *rx3, int order, const 
                const double *c0, double R0, int K, int iters, double target,
                double *out_dir, double *out_err, int32_t *choice, double *err_hist) {
     return refine_core(sp, tx3, rx3, order, faces, c0, R0, K, iters, target, NULL, 1, out_dir, out_err, choice,
-                       err_hist, NULL);
+                       err_hist, NULL, NULL, NULL);
 }
 
 /*
- * The same iteration with two test hooks that leave its arithmetic unchanged: sub_err
- * (iters x K, or NULL) receives every sub-ray's error angle per iteration, and forced (or
- * NULL) names the sub-ray each iteration keeps instead of the argmin (a negative entry
- * keeps the argmin).  Replaying another implementation's choice sequence this way gives
- * the exact FP64 state that implementation approximates, so each of its choices can be
+ * The same iteration with test hooks that leave its arithmetic unchanged: sub_err (iters x
+ * K, or NULL) receives every sub-ray's error angle per iteration; axis_log (iters, or
+ * NULL) the frame axis this implementation's own rule picks at each centre; centre_log
+ * (iters x 3, or NULL) each iteration's cone centre; and forced (or
+ * NULL) names, per iteration, the sub-ray to keep instead of the argmin (bits 0-3) and the
+ * frame axis to use instead of the rule's (bits 4-5) -- a negative entry keeps the argmin
+ * and the rule.  Replaying another implementation's logged choices this way gives the
+ * exact FP64 state that implementation approximates, so each of its choices can be
  * compared with the best sub-ray of the same cone.  stall_on = 0 disables the stalled-
  * path exit (everything else as ora_refine).
  */
 int ora_refine_ex(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
                   const double *c0, double R0, int K, int iters, double target, const int32_t *forced,
                   int stall_on, double *out_dir, double *out_err, int32_t *choice, double *err_hist,
-                  double *sub_err) {
+                  double *sub_err, int32_t *axis_log, double *centre_log) {
     return refine_core(sp, tx3, rx3, order, faces, c0, R0, K, iters, target, forced, stall_on, out_dir, out_err,
-                       choice, err_hist, sub_err);
+                       choice, err_hist, sub_err, axis_log, centre_log);
+}
+
+/*
+ * The two errors the early stop of the precise algorithm compares with its target, for a
+ * path launched along dir: out[0] = the Eq. 3 error angle (the AOD error) and out[1] = the
+ * AOA error (aoa_error).  +inf where the fixed-face trace fails.
+ */
+void ora_path_errors(void *sp, const double *tx3, const double *rx3, int order, const int32_t *faces,
+                     const double *dir, double *out) {
+    const scene *s = (const scene *)sp;
+    vec3 tx = ld(tx3), rx = ld(rx3), d = unit(ld(dir)), txk = tx;
+    for (int j = 0; j < order; ++j) txk = mirror(s, faces[j], txk);
+    out[0] = trace_planes(s, tx, rx, order, faces, d, NULL, NULL);
+    out[1] = aoa_error(s, tx, rx, order, faces, d, txk);
 }
 
 /* point-in-face: p lies inside (or on the boundary of) some triangle of face f */
@@ -1159,6 +1185,16 @@ void ora_unfold(void *sp, int order, const int32_t *faces, const double *tx3, co
         J[7 * 8 + 2 + c] = a_el; J[7 * 8 + 5 + c] = -gel[c];
     }
 #undef AT
+}
+
+/* ora_unfold's values (no Jacobian) for P paths at once: order[p], faces[8 p ..], tx/rx
+ * [3 p ..] -> vals[8 p ..].  The exact image-method delay, AOD and AOA of each face
+ * sequence (the miss terms use az = el = 0). */
+void ora_unfold_many(void *sp, int64_t P, const int32_t *order, const int32_t *faces, const double *tx,
+                     const double *rx, double *vals) {
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < P; ++p)
+        ora_unfold(sp, order[p], faces + 8 * p, tx + 3 * p, rx + 3 * p, 0.0, 0.0, vals + 8 * p, NULL);
 }
 
 int ora_num_threads(void) {

@@ -38,7 +38,8 @@ class SceneInfo(_c.Structure):
 class LaunchParams(_c.Structure):
     _fields_ = [("n_div", _i32), ("max_order", _i32), ("rx_angle_scale", _f32), ("flags", _i32),
                 ("dump_stride", _i32), ("dump_faces", _vp), ("dump_cap", _i64), ("grid_blocks", _i32),
-                ("block_threads", _i32), ("refill_min", _i32), ("launcher", _i32)]
+                ("block_threads", _i32), ("refill_min", _i32), ("launcher", _i32), ("ray_begin", _i64),
+                ("ray_end", _i64)]
 
 
 class LaunchStats(_c.Structure):
@@ -46,7 +47,8 @@ class LaunchStats(_c.Structure):
                 ("records", _i64), ("paths", _i64), ("collisions", _i64), ("ntx", _i32), ("nrx", _i32),
                 ("n_div", _i32), ("max_order", _i32), ("ms_raygen", _f32), ("ms_trace", _f32), ("ms_dedup", _f32),
                 ("trace_grid", _i32), ("trace_block", _i32), ("ms_diffract", _f32), ("wedge_tests", _i64),
-                ("diffraction_records", _i64), ("diffraction_candidates", _i64), ("candidate_cap", _i64)]
+                ("diffraction_records", _i64), ("diffraction_candidates", _i64), ("candidate_cap", _i64),
+                ("check_flags", _i64)]
 
 
 class RefineParams(_c.Structure):
@@ -61,6 +63,8 @@ class BatchConfig(_c.Structure):
 LAUNCH_SYNC = 1
 LAUNCH_TIMING = 2
 LAUNCH_DIFFRACTION = 4
+LAUNCH_RAY_RANGE = 8
+LAUNCH_RECORDS_ONLY = 16
 PATH_REFINED, PATH_FP64, PATH_TRACE_FAIL, PATH_DIFFRACTED, PATH_STALLED = 1, 2, 4, 8, 16
 
 PATH_DTYPE = np.dtype([("tx", "<i4"), ("rx", "<i4"), ("ray", "<i4"), ("order", "<i4"), ("faces", "<i4", (MAX_ORDER,)),
@@ -69,8 +73,14 @@ PATH_DTYPE = np.dtype([("tx", "<i4"), ("rx", "<i4"), ("ray", "<i4"), ("order", "
                        ("aoa", "<f4", (2,)), ("power_dbm", "<f4"), ("flags", "<i4")])
 assert PATH_DTYPE.itemsize == 128
 
+RECORD_DTYPE = np.dtype([("tx", "<i4"), ("rx", "<i4"), ("ray", "<i4"), ("order", "<i4"),
+                         ("faces", "<i4", (MAX_ORDER,)), ("err", "<f4"), ("dray", "<f4"), ("slot", "<i4"),
+                         ("pad", "<i4")])
+assert RECORD_DTYPE.itemsize == 64
+
 STATUS = {0: "SBR_OK", 1: "SBR_EINVAL", 2: "SBR_ENOMEM", 3: "SBR_ECUDA", 4: "SBR_ETIMEOUT", 5: "SBR_EOVERFLOW",
-          6: "SBR_EDEGENERATE", 7: "SBR_ECOLLISION"}
+          6: "SBR_EDEGENERATE", 7: "SBR_ECOLLISION", 8: "SBR_ECHECK"}
+CHECK_BITS = {1: "trace stack", 2: "occlusion stack", 4: "receiver stack", 8: "face id", 16: "binary-BVH stack"}
 
 # name -> (restype, argtypes); every entry point of include/sbr.h
 SIGNATURES = {
@@ -107,24 +117,27 @@ SIGNATURES = {
     "sbr_unfold_fwd": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sbr_unfold_bwd": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sbr_dedup_noalloc": (_i32, [_vp, _vp, _vp, _i64, _vp]),
+    "sbr_records_read": (_i32, [_vp, _vp, _vp, _i64, _pi64]),
+    "sbr_records_dedup": (_i32, [_vp, _vp, _vp, _i64, _i32, _i32]),
+    "sbr_paths_nonfinite": (_i32, [_vp, _vp, _pi64]),
 }
 
-_lib = None
+_libs = {}
 
 
-def library_path() -> str:
-    return _build.SO
+def library_path(checked: bool = False) -> str:
+    return _build.SO_CHECKED if checked else _build.SO
 
 
-def load(build_if_missing: bool = True):
-    """Load libsbr.so (building it first if it is missing or stale and nvcc exists)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = _build.SO
+def load(build_if_missing: bool = True, checked: bool = False):
+    """Load libsbr.so, or with checked=True the bounds-checked variant libsbr_checked.so
+    (building first if missing or stale and nvcc exists)."""
+    if checked in _libs:
+        return _libs[checked]
+    path = library_path(checked)
     if build_if_missing:
         try:
-            path = _build.build()
+            _build.build()
         except RuntimeError:
             if not os.path.exists(path):
                 raise
@@ -135,5 +148,5 @@ def load(build_if_missing: bool = True):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
+    _libs[checked] = lib
     return lib

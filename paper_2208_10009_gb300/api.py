@@ -96,10 +96,12 @@ class Paths:
 class Context:
     """One library context on one CUDA device and stream."""
 
-    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True):
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, torch_allocator: bool = True,
+                 checked: bool = False):
+        """`checked` runs the bounds-checked build of the library (SBR_CHECKED)."""
         if not torch.cuda.is_available():
             raise SbrError(3, "no CUDA device: the SBR library has no CPU path")
-        self.lib = B.load()
+        self.lib = B.load(checked=checked)
         self.device = device
         self.stream = stream or torch.cuda.current_stream(device)
         self._keep = []
@@ -198,10 +200,13 @@ class Context:
     def launch(self, scene: Scene, tx, rx: RxSet, paths: Paths, n_div: int, max_order: int,
                rx_angle_scale: float = 1.0, sync: bool = False, dump_stride: int = 0,
                dump: torch.Tensor | None = None, grid_blocks: int = 0, block_threads: int = 0,
-               timing: bool = False, refill_min: int = 0, launcher: int = 0, diffraction: bool = False):
+               timing: bool = False, refill_min: int = 0, launcher: int = 0, diffraction: bool = False,
+               ray_range: tuple[int, int] | None = None, records_only: bool = False):
         """a1-a5: ray generation, trace with reception, double-count removal.  `tx` is an
         (ntx, 3) array on the host (numpy) or the device (torch).  `diffraction` adds the
-        order-1 diffraction search."""
+        order-1 diffraction search.  `ray_range` = (begin, end) traces only those ray ids of
+        every Tx; `records_only` stops before double-count removal (read the records with
+        `records`)."""
         if isinstance(tx, torch.Tensor):
             txp, ntx = tx.data_ptr(), tx.numel() // 3
             keep = tx
@@ -209,10 +214,12 @@ class Context:
             keep = _host_f32(tx)
             txp, ntx = keep.ctypes.data, len(keep)
         flags = ((B.LAUNCH_SYNC if sync else 0) | (B.LAUNCH_TIMING if timing else 0) |
-                 (B.LAUNCH_DIFFRACTION if diffraction else 0))
+                 (B.LAUNCH_DIFFRACTION if diffraction else 0) | (B.LAUNCH_RAY_RANGE if ray_range else 0) |
+                 (B.LAUNCH_RECORDS_ONLY if records_only else 0))
+        rb, re_ = (int(ray_range[0]), int(ray_range[1])) if ray_range else (0, 0)
         prm = B.LaunchParams(n_div, max_order, rx_angle_scale, flags, dump_stride,
                              _ptr(dump), 0 if dump is None else dump.numel(), grid_blocks, block_threads,
-                             refill_min, launcher)
+                             refill_min, launcher, rb, re_)
         self._check(self.lib.sbr_launch(self.handle, scene.handle, txp, ntx, rx.handle, ctypes.byref(prm),
                                         paths.handle))
         del keep
@@ -246,6 +253,12 @@ class Context:
         self._check(self.lib.sbr_batch_refine(self.handle, scene.handle, paths.handle, ctypes.byref(prm),
                                               ctypes.byref(cfg)))
 
+    def paths_nonfinite(self, paths: Paths) -> int:
+        """Valid paths with a non-finite output (device scan; 0 when the outputs are sound)."""
+        n = ctypes.c_int64()
+        self._check(self.lib.sbr_paths_nonfinite(self.handle, paths.handle, ctypes.byref(n)))
+        return n.value
+
     def paths_count(self, paths: Paths) -> int:
         n = ctypes.c_int64()
         self._check(self.lib.sbr_paths_count(self.handle, paths.handle, ctypes.byref(n)))
@@ -265,6 +278,34 @@ class Context:
         w = ctypes.c_int64()
         self._check(self.lib.sbr_query(self.handle, paths.handle, _ptr(out) if cap else None, cap, ctypes.byref(w)))
         return out[: w.value] if not isinstance(out, torch.Tensor) else (out, w.value)
+
+    def records(self, paths: Paths, out: torch.Tensor | None = None):
+        """The reception records of the container's last launch (before double-count
+        removal): a numpy RECORD_DTYPE array, or (out, count) when `out` is a device uint8
+        tensor of 64 bytes per record."""
+        if out is None:
+            n = int(self.launch_stats(paths)["records"])
+            out = np.zeros(min(n, paths.record_cap), B.RECORD_DTYPE)
+            cap = len(out)
+        else:
+            cap = out.numel() // 64
+        w = ctypes.c_int64()
+        self._check(self.lib.sbr_records_read(self.handle, paths.handle, _ptr(out) if cap else None, cap,
+                                              ctypes.byref(w)))
+        return out[: w.value] if not isinstance(out, torch.Tensor) else (out, w.value)
+
+    def records_dedup(self, paths: Paths, records, count: int | None = None, rank: int = 0, world: int = 1):
+        """a5 on a given record set (host RECORD_DTYPE array or device uint8 tensor of 64-byte
+        records): the container's paths become the unique paths of the (tx, rx) pairs that
+        shard `rank` of `world` owns ((tx * nrx + rx) % world == rank)."""
+        if isinstance(records, torch.Tensor):
+            n = records.numel() // 64 if count is None else count
+            p = records.data_ptr()
+        else:
+            records = np.ascontiguousarray(records.astype(B.RECORD_DTYPE, copy=False))
+            n = len(records) if count is None else count
+            p = records.ctypes.data
+        self._check(self.lib.sbr_records_dedup(self.handle, paths.handle, p if n else None, n, rank, world))
 
     def paths_import(self, paths: Paths, records: np.ndarray, tx, rx: RxSet, n_div: int):
         recs = np.ascontiguousarray(records.astype(B.PATH_DTYPE, copy=False))

@@ -2,7 +2,10 @@
 
 Each translation unit is compiled in parallel; the shared library links the CUDA runtime
 statically.  The output lives in ``paper_2208_10009_gb300/_lib/`` (git-ignored) and is
-rebuilt when any source or header is newer than it.
+rebuilt when any source or header is newer than it.  A second variant,
+``libsbr_checked.so``, is compiled with -DSBR_CHECKED: device bounds checks on traversal
+stacks and face ids that report through the launch's status word (SBR_ECHECK) instead of
+faulting.
 """
 from __future__ import annotations
 
@@ -17,9 +20,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 SO = os.path.join(OUT, "libsbr.so")
+SO_CHECKED = os.path.join(OUT, "libsbr_checked.so")
 SOURCES = ["capi.cu", "host_geometry.cpp", "host_wedges.cpp", "host_faces.cpp", "kernels_trace.cu", "kernels_diffract.cu",
            "kernels_paths.cu", "kernels_refine.cu", "kernels_unfold.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+VARIANTS = {SO: [], SO_CHECKED: ["-DSBR_CHECKED"]}
 
 
 def nvcc() -> str:
@@ -34,40 +39,48 @@ def _flags():
                    "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
 
 
-def _stale() -> bool:
-    if not os.path.exists(SO):
+def _stale(so: str) -> bool:
+    if not os.path.exists(so):
         return True
-    t = os.path.getmtime(SO)
+    t = os.path.getmtime(so)
     deps = glob.glob(os.path.join(CSRC, "*")) + [os.path.join(ROOT, "include", "sbr.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every translation unit and link libsbr.so; returns its path."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, checked: bool = True) -> str:
+    """Compile every translation unit of each stale variant (the checked one too unless
+    checked=False) in one parallel pass and link the libraries; returns libsbr.so's path."""
+    todo = [so for so in VARIANTS if (so == SO or checked) and (force or _stale(so))]
+    if not todo:
         return SO
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-        cmd = [cc] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
-        if src.endswith(".cpp"):
-            cmd = [cc] + _flags() + ["-x", "cu", "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job):
+        so, src = job
+        sub = os.path.join(OUT, "checked") if so == SO_CHECKED else OUT
+        os.makedirs(sub, exist_ok=True)
+        obj = os.path.join(sub, os.path.splitext(src)[0] + ".o")
+        cmd = [cc] + _flags() + VARIANTS[so] + (["-x", "cu"] if src.endswith(".cpp") else []) + \
+            ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         if verbose and (r.stdout or r.stderr):
             print(r.stdout, r.stderr)
-        return obj
+        return so, obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = SO + ".tmp"
-    r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, SO)
+    jobs = [(so, src) for so in todo for src in SOURCES]
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), max(os.cpu_count() or 4, 4))) as ex:
+        done = list(ex.map(compile_one, jobs))
+    for so in todo:
+        objs = [o for s, o in done if s == so]
+        tmp = so + ".tmp"
+        r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"], capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, so)
     return SO
 
 

@@ -1,11 +1,14 @@
 // capi.cu -- the C ABI declared in include/sbr.h: handles, validation, memory, and the
 // order in which the kernels of the SBR hot path are enqueued.
 #include <algorithm>
+#include <cstddef>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include "nvtx_ranges.h"
 #include "sbr_internal.h"
 
 using namespace sbr;
@@ -490,6 +493,12 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     sc->dev.wnodes = d_wn;
     sc->dev.wedge_bvh_ids = d_wid;
     sc->dev.nw = nw;
+    sc->dev.status = nullptr;
+    sc->dev.stack_limit = kStack4;
+#ifdef SBR_CHECKED
+    if (const char *lim = std::getenv("SBR_CHECKED_STACK_LIMIT"))
+        sc->dev.stack_limit = std::max(1, std::min(kStack4, std::atoi(lim)));
+#endif
     sc->wedges = std::move(wl);
     sc->info.num_wedges = nw;
     sc->info.num_triangles = nt;
@@ -700,6 +709,24 @@ static sbr_status ensure_tx(sbr_ctx *ctx, sbr_paths *p, const float *tx, int32_t
     return copy_points(ctx, p->tx, tx, ntx);
 }
 
+static sbr_status report_checks(sbr_ctx *ctx, long long flags, const char *where);
+
+static DedupArgs dedup_args(sbr_ctx *ctx, sbr_paths *paths, int nrx, int rank, int world) {
+    DedupArgs d;
+    d.recs = paths->recs;
+    d.rec_cap = paths->record_cap;
+    d.table = paths->table;
+    d.slots = paths->table_slots;
+    d.paths = paths->paths;
+    d.path_cap = paths->path_cap;
+    d.dirs = static_cast<const float4 *>(ctx->dirs);
+    d.counters = paths->counters;
+    d.nrx = nrx;
+    d.shard_rank = rank;
+    d.shard_world = world;
+    return d;
+}
+
 sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int32_t ntx, const sbr_rxset *rx,
                       const sbr_launch_params *prm, sbr_paths *paths) {
     if (!ctx || !scene || !tx || !rx || !prm || !paths) return fail(ctx, SBR_EINVAL, "sbr_launch: null argument");
@@ -717,6 +744,14 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
         if (prm->dump_cap < (int64_t)ntx * per * (prm->max_order + 1))
             return fail(ctx, SBR_EINVAL, "sbr_launch: dump_cap smaller than ntx * ceil(N / stride) * (max_order + 1)");
     }
+    const int64_t N = rays_for_launcher(prm->n_div, prm->launcher);
+    int64_t ray_begin = 0, ray_count = N;
+    if (prm->flags & SBR_LAUNCH_RAY_RANGE) {
+        if (prm->ray_begin < 0 || prm->ray_end < prm->ray_begin || prm->ray_end > N)
+            return fail(ctx, SBR_EINVAL, "sbr_launch: ray range must satisfy 0 <= ray_begin <= ray_end <= N");
+        ray_begin = prm->ray_begin;
+        ray_count = prm->ray_end - prm->ray_begin;
+    }
     DeviceGuard g(ctx->device);
     sbr_status st = ensure_tx(ctx, paths, tx, ntx);
     if (st != SBR_OK) return st;
@@ -724,18 +759,22 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     if (timing && !ctx->ev[0])
         for (auto &e : ctx->ev) SBR_CUDA(cudaEventCreate(&e));
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[0], ctx->stream));
-    st = ensure_dirs(ctx, prm->n_div, prm->launcher);
+    {
+        Range r("sbr_launch: raygen");
+        st = ensure_dirs(ctx, prm->n_div, prm->launcher);
+    }
     if (st != SBR_OK) return st;
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[1], ctx->stream));
-    const int64_t N = rays_for_launcher(prm->n_div, prm->launcher);
     SBR_CUDA(cudaMemsetAsync(paths->counters, 0, kNumCounters * sizeof(long long), ctx->stream));
     TraceArgs a;
     a.scene = scene->dev;
+    a.scene.status = reinterpret_cast<unsigned long long *>(paths->counters + kErrorFlags);
     a.rx = rx->dev;
     a.dirs = static_cast<const float4 *>(ctx->dirs);
     a.tx = paths->tx;
     a.ntx = ntx;
-    a.nrays_per_tx = N;
+    a.nrays_per_tx = ray_count;
+    a.ray_begin = ray_begin;
     a.max_order = prm->max_order;
     double cone = prm->rx_angle_scale * sbr_theta_launch(prm->n_div);
     a.cone = (float)cone;
@@ -752,16 +791,20 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     if (block % 32 != 0 || block > 128)
         return fail(ctx, SBR_EINVAL, "sbr_launch: block_threads must be a multiple of 32, at most 128");
     int grid = prm->grid_blocks > 0 ? prm->grid_blocks : ctx->num_sms * trace_blocks_per_sm(block);
-    SBR_CUDA(launch_trace(a, grid, block, ctx->stream));
+    {
+        Range r("sbr_launch: trace + reception");
+        SBR_CUDA(launch_trace(a, grid, block, ctx->stream));
+    }
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[2], ctx->stream));
     if (prm->flags & SBR_LAUNCH_DIFFRACTION) {
         DiffractArgs df;
-        df.scene = scene->dev;
+        df.scene = a.scene;
         df.rx = rx->dev;
         df.dirs = a.dirs;
         df.tx = paths->tx;
         df.ntx = ntx;
-        df.nrays_per_tx = N;
+        df.nrays_per_tx = ray_count;
+        df.ray_begin = ray_begin;
         df.cone = a.cone;
         df.tan_cone = a.tan_cone;
         df.recs = paths->recs;
@@ -770,21 +813,17 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
         // the candidate list borrows the dedup table, which is cleared after this step
         df.cand = reinterpret_cast<float4 *>(paths->table);
         df.cand_cap = paths->table_slots * 5 / 8;
+        Range r("sbr_launch: diffraction");
         SBR_CUDA(launch_diffract(df, ctx->num_sms, ctx->stream));
     }
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[4], ctx->stream));
     paths->trace_grid = grid;
     paths->trace_block = block;
-    DedupArgs d;
-    d.recs = paths->recs;
-    d.rec_cap = paths->record_cap;
-    d.table = paths->table;
-    d.slots = paths->table_slots;
-    d.paths = paths->paths;
-    d.path_cap = paths->path_cap;
-    d.dirs = a.dirs;
-    d.counters = paths->counters;
-    SBR_CUDA(launch_dedup(d, ctx->num_sms, ctx->stream));
+    if (!(prm->flags & SBR_LAUNCH_RECORDS_ONLY)) {
+        DedupArgs d = dedup_args(ctx, paths, rx->dev.nrx, 0, 1);
+        Range r("sbr_launch: dedup");
+        SBR_CUDA(launch_dedup(d, ctx->num_sms, ctx->stream));
+    }
     if (timing) SBR_CUDA(cudaEventRecord(ctx->ev[3], ctx->stream));
     paths->timed = timing;
     paths->ntx = ntx;
@@ -794,6 +833,8 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     paths->max_order = prm->max_order;
     paths->rx = rx;
     paths->alpha = prm->rx_angle_scale;
+    paths->ray_begin = ray_begin;
+    paths->ray_count = ray_count;
     paths->pair_cap = -1;   // per-pair buckets are stale
     if (prm->flags & SBR_LAUNCH_SYNC) {
         sbr_launch_stats s;
@@ -803,6 +844,8 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
             return fail(ctx, SBR_EOVERFLOW, "sbr_launch: " + std::to_string(s.records) + " records / " +
                                                 std::to_string(s.paths) + " paths exceed the container");
         if (s.collisions) return fail(ctx, SBR_ECOLLISION, "sbr_launch: dedup hash collision");
+        st = report_checks(ctx, s.check_flags, "sbr_launch");
+        if (st != SBR_OK) return st;
     }
     return SBR_OK;
 }
@@ -813,7 +856,7 @@ sbr_status sbr_launch_get_stats(sbr_ctx *ctx, const sbr_paths *paths, sbr_launch
     long long c[kNumCounters];
     SBR_CUDA(cudaMemcpyAsync(c, paths->counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
     SBR_CUDA(cudaStreamSynchronize(ctx->stream));
-    out->rays = (int64_t)paths->ntx * std::max<int64_t>(rays_for_launcher(std::max(paths->n_div, 1), paths->launcher), 0);
+    out->rays = (int64_t)paths->ntx * paths->ray_count;
     out->segments = c[kSegments];
     out->node_visits = c[kNodeVisits];
     out->tri_tests = c[kTriTests];
@@ -838,6 +881,70 @@ sbr_status sbr_launch_get_stats(sbr_ctx *ctx, const sbr_paths *paths, sbr_launch
     out->candidate_cap = paths->table_slots * 5 / 8;
     out->trace_grid = paths->trace_grid;
     out->trace_block = paths->trace_block;
+    out->check_flags = c[kErrorFlags];
+    return SBR_OK;
+}
+
+// SBR_ECHECK with the failed checks named, when a container's status word has bits set
+static sbr_status report_checks(sbr_ctx *ctx, long long flags, const char *where) {
+    if (!flags) return SBR_OK;
+    static const char *names[] = {"trace stack", "occlusion stack", "receiver stack", "face id", "binary-BVH stack"};
+    std::string m = std::string(where) + ": device bounds checks failed:";
+    for (int b = 0; b < 5; ++b)
+        if (flags & (1LL << b)) m += std::string(" ") + names[b];
+    return fail(ctx, SBR_ECHECK, m);
+}
+
+// ------------------------------------------------------------------------------ records
+static_assert(sizeof(sbr_reception_record) == sizeof(RecDev), "reception record layout");
+static_assert(offsetof(sbr_reception_record, err) == offsetof(RecDev, err), "reception record layout");
+static_assert(offsetof(sbr_reception_record, slot) == offsetof(RecDev, slot), "reception record layout");
+
+sbr_status sbr_records_read(sbr_ctx *ctx, const sbr_paths *paths, sbr_reception_record *out, int64_t cap,
+                            int64_t *written) {
+    if (!ctx || !paths || !written || cap < 0 || (cap > 0 && !out))
+        return fail(ctx, SBR_EINVAL, "sbr_records_read: null argument or negative cap");
+    DeviceGuard g(ctx->device);
+    long long c = 0;
+    SBR_CUDA(cudaMemcpyAsync(&c, paths->counters + kRecords, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
+    SBR_CUDA(cudaStreamSynchronize(ctx->stream));
+    int64_t n = std::min<int64_t>(std::min<int64_t>(c, paths->record_cap), cap);
+    if (n > 0) {
+        cudaMemcpyKind kind = is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        SBR_CUDA(cudaMemcpyAsync(out, paths->recs, (size_t)n * sizeof(RecDev), kind, ctx->stream));
+        SBR_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    *written = n;
+    return SBR_OK;
+}
+
+sbr_status sbr_records_dedup(sbr_ctx *ctx, sbr_paths *paths, const sbr_reception_record *in, int64_t count,
+                             int32_t rank, int32_t world) {
+    if (!ctx || !paths || count < 0 || (count > 0 && !in))
+        return fail(ctx, SBR_EINVAL, "sbr_records_dedup: null argument or negative count");
+    if (world < 1 || rank < 0 || rank >= world)
+        return fail(ctx, SBR_EINVAL, "sbr_records_dedup: need 0 <= rank < world");
+    if (!paths->rx || paths->ntx < 1 || paths->n_div < 1)
+        return fail(ctx, SBR_EINVAL, "sbr_records_dedup: the container holds no launch");
+    if (count > paths->record_cap)
+        return fail(ctx, SBR_EOVERFLOW, "sbr_records_dedup: " + std::to_string(count) + " records exceed record_cap");
+    DeviceGuard g(ctx->device);
+    if (!(ctx->dirs_valid && ctx->dirs_n == paths->n_div && ctx->dirs_launcher == paths->launcher)) {
+        sbr_status st = ensure_dirs(ctx, paths->n_div, paths->launcher);   // rough launch directions
+        if (st != SBR_OK) return st;
+    }
+    if (count > 0) {
+        cudaMemcpyKind kind = is_device_ptr(in) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        SBR_CUDA(cudaMemcpyAsync(paths->recs, in, (size_t)count * sizeof(RecDev), kind, ctx->stream));
+    }
+    SBR_CUDA(launch_records_reset(paths->counters, count, ctx->stream));
+    DedupArgs d = dedup_args(ctx, paths, paths->nrx, rank, world);
+    {
+        Range r("sbr_records_dedup: dedup");
+        SBR_CUDA(launch_dedup(d, ctx->num_sms, ctx->stream));
+    }
+    paths->pair_cap = -1;
+    paths->timed = false;
     return SBR_OK;
 }
 
@@ -851,6 +958,7 @@ static sbr_status refine_args(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *p
     if (prm->max_iters < 0 || prm->max_iters > 200) return fail(ctx, SBR_EINVAL, "refine: max_iters out of [0, 200]");
     if (!paths->rx || paths->ntx < 1) return fail(ctx, SBR_EINVAL, "refine: container holds no launch");
     A.scene = scene->dev;
+    A.scene.status = reinterpret_cast<unsigned long long *>(paths->counters + kErrorFlags);
     A.tx = paths->tx;
     A.rx = paths->rx->dev.by_id;
     A.paths = paths->paths;
@@ -892,7 +1000,10 @@ sbr_status sbr_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *paths, co
     DeviceGuard g(ctx->device);
     int nb = 1;
     refine_kernel_attrs(nullptr, 128, &nb, false, 0);
-    SBR_CUDA(launch_refine(A, ctx->num_sms * nb, 128, ctx->stream));
+    {
+        Range r("sbr_refine: iterations + validity + outputs");
+        SBR_CUDA(launch_refine(A, ctx->num_sms * nb, 128, ctx->stream));
+    }
     return SBR_OK;
 }
 
@@ -923,17 +1034,23 @@ sbr_status sbr_refine_pair(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *path
         pa.pair_count = paths->pair_off;
         pa.pair_idx = paths->pair_off + npairs + 1;
         SBR_CUDA(launch_pair_bucket(pa, ctx->stream));
+        // one host copy of every pair's range per launch, so that later calls size their
+        // grid without a device round trip
+        paths->pair_host.resize((size_t)npairs + 1);
+        SBR_CUDA(cudaMemcpyAsync(paths->pair_host.data(), paths->pair_off, sizeof(int) * ((size_t)npairs + 1),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        SBR_CUDA(cudaStreamSynchronize(ctx->stream));
         paths->pair_cap = paths->path_cap;
     }
-    int be[2];
     int p = tx * paths->nrx + rx;
-    SBR_CUDA(cudaMemcpyAsync(be, paths->pair_off + p, sizeof(be), cudaMemcpyDeviceToHost, ctx->stream));
-    SBR_CUDA(cudaStreamSynchronize(ctx->stream));
-    int count = be[1] - be[0];
+    int count = paths->pair_host[p + 1] - paths->pair_host[p];
     if (count <= 0) return SBR_OK;
     A.range = paths->pair_off + p;
     A.index = paths->pair_off + npairs + 1;
-    SBR_CUDA(launch_refine(A, (count + 127) / 128, 128, ctx->stream));
+    {
+        Range r("sbr_refine_pair: iterations + validity + outputs");
+        SBR_CUDA(launch_refine(A, (count + 127) / 128, 128, ctx->stream));
+    }
     return SBR_OK;
 }
 
@@ -954,7 +1071,10 @@ sbr_status sbr_batch_refine(sbr_ctx *ctx, const sbr_scene *scene, sbr_paths *pat
     if (cfg && cfg->blocks_per_sm > 0) nb = std::min(nb, cfg->blocks_per_sm);
     A.chunk = lanes;
     if (lanes == 1) A.split_min = 0;   // the one-lane form runs with the unfold and FP64 tail kernels
-    SBR_CUDA(launch_batch_refine(A, ctx->num_sms * nb, block, ctx->stream));
+    {
+        Range r("sbr_batch_refine: unfold, iterations, FP64 tail, validity + outputs");
+        SBR_CUDA(launch_batch_refine(A, ctx->num_sms * nb, block, ctx->stream));
+    }
     return SBR_OK;
 }
 
@@ -974,6 +1094,15 @@ sbr_status sbr_query(sbr_ctx *ctx, const sbr_paths *paths, sbr_path_record *out,
     int64_t n = 0;
     sbr_status st = sbr_paths_count(ctx, paths, &n);
     if (st != SBR_OK) return st;
+    if (SBR_CHECKED_BUILD) {
+        long long flags = 0;
+        DeviceGuard g0(ctx->device);
+        SBR_CUDA(cudaMemcpyAsync(&flags, paths->counters + kErrorFlags, sizeof(flags), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+        SBR_CUDA(cudaStreamSynchronize(ctx->stream));
+        st = report_checks(ctx, flags, "sbr_query");
+        if (st != SBR_OK) return st;
+    }
     n = std::min(n, cap);
     DeviceGuard g(ctx->device);
     if (n > 0) {
@@ -982,6 +1111,17 @@ sbr_status sbr_query(sbr_ctx *ctx, const sbr_paths *paths, sbr_path_record *out,
         SBR_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     *written = n;
+    return SBR_OK;
+}
+
+sbr_status sbr_paths_nonfinite(sbr_ctx *ctx, const sbr_paths *paths, int64_t *count) {
+    if (!ctx || !paths || !count) return fail(ctx, SBR_EINVAL, "sbr_paths_nonfinite: null argument");
+    DeviceGuard g(ctx->device);
+    SBR_CUDA(launch_nonfinite_scan(paths->paths, paths->counters, paths->path_cap, ctx->num_sms, ctx->stream));
+    long long c = 0;
+    SBR_CUDA(cudaMemcpyAsync(&c, paths->counters + kNonFinite, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
+    SBR_CUDA(cudaStreamSynchronize(ctx->stream));
+    *count = c;
     return SBR_OK;
 }
 

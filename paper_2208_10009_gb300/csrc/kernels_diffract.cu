@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(128) diffract_candidates(DiffractArgs A) {
         const long long i = base + lane;
         bool done = i >= total, tail = false;
         const int txi = done ? 0 : (int)(i / A.nrays_per_tx);
-        const int ray = done ? 0 : (int)(i - (long long)txi * A.nrays_per_tx);
+        const int ray = done ? 0 : (int)(A.ray_begin + (i - (long long)txi * A.nrays_per_tx));
         const float3 o = f3(__ldg(A.tx + txi));
         const float3 d = f3(__ldg(A.dirs + ray));
         const RayPre r = make_ray(o, d);
@@ -137,7 +137,10 @@ __global__ void __launch_bounds__(128) diffract_candidates(DiffractArgs A) {
                     int4 refs = __ldg(reinterpret_cast<const int4 *>(nd + 3));
                     bool in0 = cone_box(p.x, p.y, p.z, p.w, q.x, q.y, r, od, A.tan_cone);
                     bool in1 = cone_box(q.z, q.w, t.x, t.y, t.z, t.w, r, od, A.tan_cone);
-                    if (in0 && in1) {
+                    if (in0 && in1 && SBR_CHECKED_ON && sp >= min(S.stack_limit, kStackDepth)) {
+                        check_fail(S, SBR_CHECK_BVH2_STACK);
+                        done = true;
+                    } else if (in0 && in1) {
                         stack[sp++] = refs.y;
                         node = refs.x;
                     } else if (in0) {

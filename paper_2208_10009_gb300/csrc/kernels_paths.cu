@@ -91,6 +91,7 @@ __global__ void dedup_select(DedupArgs a) {
         if (r.slot < 0) continue;
         if (vals[r.slot] != rec_value(r)) continue;
         winner[r.slot] = (int)i;
+        if (a.shard_world > 1 && (r.tx * a.nrx + r.rx) % a.shard_world != a.shard_rank) continue;
         unsigned long long p = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kPaths), 1ULL);
         if ((long long)p >= a.path_cap) continue;
         sbr_path_record out;
@@ -138,6 +139,46 @@ cudaError_t launch_dedup(const DedupArgs &a, int num_sms, cudaStream_t s) {
     dedup_insert<<<grid, 256, 0, s>>>(a);
     dedup_select<<<grid, 256, 0, s>>>(a);
     dedup_verify<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void records_reset(long long *counters, long long n) {
+    counters[kRecords] = n;
+    counters[kPaths] = 0;
+    counters[kCollisions] = 0;
+}
+
+cudaError_t launch_records_reset(long long *counters, long long n, cudaStream_t s) {
+    records_reset<<<1, 1, 0, s>>>(counters, n);
+    return cudaGetLastError();
+}
+
+// Valid paths with a non-finite output: an output scan (NaN / Inf in a valid path's
+// direction, error angle, delay, angles or power means a numerical fault).
+__device__ __forceinline__ bool finite_path(const sbr_path_record &p) {
+    bool ok = isfinite(p.dir[0]) && isfinite(p.dir[1]) && isfinite(p.dir[2]) && isfinite(p.err) && isfinite(p.delay);
+    ok = ok && isfinite(p.aod[0]) && isfinite(p.aod[1]) && isfinite(p.aoa[0]) && isfinite(p.aoa[1]);
+    return ok && isfinite(p.power_dbm);
+}
+
+__global__ void nonfinite_scan(const sbr_path_record *paths, long long *counters, long long cap) {
+    long long n = counters[kPaths];
+    if (n > cap) n = cap;
+    unsigned bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const sbr_path_record &p = paths[i];
+        if (p.valid && !finite_path(p)) ++bad;
+    }
+    bad = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && bad)
+        atomicAdd(reinterpret_cast<unsigned long long *>(counters + kNonFinite), (unsigned long long)bad);
+}
+
+cudaError_t launch_nonfinite_scan(const sbr_path_record *paths, long long *counters, int64_t path_cap, int num_sms,
+                                  cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counters + kNonFinite, 0, sizeof(long long), s);
+    if (e != cudaSuccess) return e;
+    nonfinite_scan<<<num_sms * 4, 256, 0, s>>>(paths, counters, path_cap);
     return cudaGetLastError();
 }
 

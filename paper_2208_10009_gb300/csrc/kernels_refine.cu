@@ -10,6 +10,7 @@
 // traces each through the path's fixed face planes, evaluates Eq. 3 at Rx, keeps the
 // smallest (lowest k on ties) and shrinks R by the pattern's factor.  Iterations run in
 // FP32 while R >= fp64_below and in FP64 after that.
+#include "nvtx_ranges.h"
 #include "sbr_device.cuh"
 
 namespace sbr {
@@ -344,26 +345,36 @@ __device__ __forceinline__ void sincos_sub32(float x, float &s, float &c) {
 }
 
 // sub-cone frame: u = normalize(c x e), e the world axis with the smallest |c_i| (lowest
-// index on ties), v = c x u
-__device__ __forceinline__ void frame32(float3 c, float3 &u, float3 &v) {
+// index on ties), v = c x u.  frame_axis* is that axis (0, 1, 2), also written to the
+// choice log beside the argmin.
+__device__ __forceinline__ int frame_axis32(float3 c) {
     float ax = fabsf(c.x), ay = fabsf(c.y), az = fabsf(c.z);
-    float3 e = make_float3(1, 0, 0);
-    if (ay < ax && ay <= az) e = make_float3(0, 1, 0);
-    else if (az < ax && az < ay) e = make_float3(0, 0, 1);
+    return (ay < ax && ay <= az) ? 1 : ((az < ax && az < ay) ? 2 : 0);
+}
+
+__device__ __forceinline__ int frame_axis64(dvec3 c) {
+    double ax = fabs(c.x), ay = fabs(c.y), az = fabs(c.z);
+    return (ay < ax && ay <= az) ? 1 : ((az < ax && az < ay) ? 2 : 0);
+}
+
+__device__ __forceinline__ void frame32(float3 c, float3 &u, float3 &v) {
+    const int a = frame_axis32(c);
+    const float3 e = make_float3(a == 0, a == 1, a == 2);
     u = cross(c, e);
     u = u * (1.0f / sqrtf(dot(u, u)));
     v = cross(c, u);
 }
 
 __device__ __forceinline__ void frame64(dvec3 c, dvec3 &u, dvec3 &v) {
-    double ax = fabs(c.x), ay = fabs(c.y), az = fabs(c.z);
-    dvec3 e = dv(1, 0, 0);
-    if (ay < ax && ay <= az) e = dv(0, 1, 0);
-    else if (az < ax && az < ay) e = dv(0, 0, 1);
+    const int a = frame_axis64(c);
+    const dvec3 e = dv(a == 0, a == 1, a == 2);
     u = dcross(c, e);
     u = u * (1.0 / dnorm(u));
     v = dcross(c, u);
 }
+
+// choice-log entry of one iteration: the argmin sub-ray in bits 0-3, the frame axis in 4-5
+__device__ __forceinline__ int8_t choice_entry(int bk, int axis) { return (int8_t)(bk | (axis << 4)); }
 
 // One iteration: returns the chosen sub-ray (or -1 if all are invalid); updates the cone
 // centre and its |d x W|^2 and d . W.  The FP32 phase keeps this state in FP32 registers
@@ -488,6 +499,10 @@ __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p)
             bool in1 = px >= b.z - tol && py >= b.w - tol && pz >= c.x - tol && px <= c.y + tol && py <= c.z + tol &&
                        pz <= c.w + tol;
             if (in0 && in1) {
+                if (SBR_CHECKED_ON && sp >= min(S.stack_limit, kStackDepth)) {
+                    check_fail(S, SBR_CHECK_BVH2_STACK);
+                    return false;
+                }
                 stack[sp++] = refs.y;
                 node = refs.x;
                 continue;
@@ -739,12 +754,13 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
             keyf = key32(uf, g.k, cf, dwf);
             while (it < A.max_iters && !reached32(A, g, uf, cf, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
                    !(Rf < A.fp64_below_f)) {
+                const int ax = A.choice_log ? frame_axis32(cf) : 0;
                 const int bk = iterate32(uf, g.k, A.K, off, Rf, cf, keyf, dwf);
                 if (bk < 0) {
                     fail = true;
                     break;
                 }
-                if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+                if (A.choice_log) A.choice_log[pi * A.max_iters + it] = choice_entry(bk, ax);
                 Rf *= shrinkf;
                 ++it;
             }
@@ -761,6 +777,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
                 dw = dwf;
             }
             while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
+                const int ax = A.choice_log ? frame_axis64(c) : 0;
                 const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
                 if (bk < 0) {
                     fail = true;
@@ -768,7 +785,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
                 }
                 flags |= SBR_PATH_FP64;
                 fp64 = true;
-                if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+                if (A.choice_log) A.choice_log[pi * A.max_iters + it] = choice_entry(bk, ax);
                 R *= shrink;
                 ++it;
             }
@@ -1037,13 +1054,14 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
             keyf = key32(uf, g.k, cf, dwf);
             while (it < A.max_iters && !reached32(A, g, uf, cf, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
                    !(Rf < A.fp64_below_f)) {
+                const int ax = A.choice_log ? frame_axis32(cf) : 0;
                 const int bk = G == 1 ? iterate32(uf, g.k, A.K, off, Rf, cf, keyf, dwf)
                                       : group_iterate32<G>(uf, g.k, A.K, off, Rf, cf, keyf, dwf, gl, gmask);
                 if (bk < 0) {
                     fail = true;
                     break;
                 }
-                if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+                if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = choice_entry(bk, ax);
                 Rf *= shrinkf;
                 ++it;
             }
@@ -1080,6 +1098,7 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
                 dw = dwf;
             }
             while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
+                const int ax = A.choice_log ? frame_axis64(c) : 0;
                 const int bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
                 if (bk < 0) {
                     fail = true;
@@ -1087,7 +1106,7 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
                 }
                 flags |= SBR_PATH_FP64;
                 fp64 = true;
-                if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+                if (A.choice_log && gl == 0) A.choice_log[pi * A.max_iters + it] = choice_entry(bk, ax);
                 R *= shrink;
                 ++it;
             }
@@ -1170,6 +1189,7 @@ __global__ void __launch_bounds__(128) batch_refine64_kernel(RefineArgs A) {
             dw = dwf;
         }
         while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
+            const int ax = A.choice_log ? frame_axis64(c) : 0;
             const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
             if (bk < 0) {
                 fail = true;
@@ -1177,7 +1197,7 @@ __global__ void __launch_bounds__(128) batch_refine64_kernel(RefineArgs A) {
             }
             flags |= SBR_PATH_FP64;
             fp64 = true;
-            if (A.choice_log) A.choice_log[pi * A.max_iters + it] = (int8_t)bk;
+            if (A.choice_log) A.choice_log[pi * A.max_iters + it] = choice_entry(bk, ax);
             R *= shrink;
             ++it;
         }
@@ -1309,12 +1329,18 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
     }
     e = cudaMemsetAsync(a.order_cnt, 0, 64 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    batch_unfold_kernel<<<sms * unf_blocks, 128, 0, s>>>(a);
-    switch (a.chunk) {
-        case 1: batch_refine_kernel<1><<<grid, block, 0, s>>>(a); break;
-        case 8: batch_refine_kernel<8><<<grid, block, 0, s>>>(a); break;
-        case 32: batch_refine_kernel<32><<<grid, block, 0, s>>>(a); break;
-        default: batch_refine_kernel<16><<<grid, block, 0, s>>>(a); break;
+    {
+        Range r("batch refine: plane unfolding");
+        batch_unfold_kernel<<<sms * unf_blocks, 128, 0, s>>>(a);
+    }
+    {
+        Range r("batch refine: iterations (work queue)");
+        switch (a.chunk) {
+            case 1: batch_refine_kernel<1><<<grid, block, 0, s>>>(a); break;
+            case 8: batch_refine_kernel<8><<<grid, block, 0, s>>>(a); break;
+            case 32: batch_refine_kernel<32><<<grid, block, 0, s>>>(a); break;
+            default: batch_refine_kernel<16><<<grid, block, 0, s>>>(a); break;
+        }
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1323,13 +1349,19 @@ cudaError_t launch_batch_refine(const RefineArgs &a, int grid, int block, cudaSt
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tail_blocks, batch_refine64_kernel, 128, 0);
         if (tail_blocks < 1) tail_blocks = 1;
     }
-    batch_refine64_kernel<<<sms * tail_blocks, 128, 0, s>>>(a);
+    {
+        Range r("batch refine: FP64 tail");
+        batch_refine64_kernel<<<sms * tail_blocks, 128, 0, s>>>(a);
+    }
     static int fin_blocks = 0;
     if (!fin_blocks) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fin_blocks, batch_finalize_kernel, 128, 0);
         if (fin_blocks < 1) fin_blocks = 1;
     }
-    batch_finalize_kernel<<<sms * fin_blocks, 128, 0, s>>>(a);
+    {
+        Range r("batch refine: validity + outputs");
+        batch_finalize_kernel<<<sms * fin_blocks, 128, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

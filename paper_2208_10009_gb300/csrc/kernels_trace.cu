@@ -242,6 +242,10 @@ __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, c
             const float tnz[4] = {nz01.x, nz01.y, nz23.x, nz23.y}, tfz[4] = {fz01.x, fz01.y, fz23.x, fz23.y};
             const int rf[4] = {refs.x, refs.y, refs.z, refs.w};
             int next = 0x7fffffff;
+            if (SBR_CHECKED_ON && sp + 3 > a.scene.stack_limit) {   // up to three pushes follow
+                check_fail(a.scene, SBR_CHECK_RX_STACK);
+                return;
+            }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 float tn = max3f(tnx[c], tny[c], fmaxf(tnz[c], 0.0f));
@@ -325,7 +329,7 @@ __global__ void __launch_bounds__(128, 7) trace_kernel(TraceArgs a) {
                 long long gid = (long long)base + __popc(need & lt_mask);
                 if (gid < total) {
                     st.txi = (int)(gid / a.nrays_per_tx);
-                    st.ray = (int)(gid - (long long)st.txi * a.nrays_per_tx);
+                    st.ray = (int)(a.ray_begin + (gid - (long long)st.txi * a.nrays_per_tx));
                     st.o = f3(__ldg(a.tx + st.txi));
                     st.d = f3(__ldg(a.dirs + st.ray));
                     st.L = 0.0f;
@@ -353,7 +357,10 @@ __global__ void __launch_bounds__(128, 7) trace_kernel(TraceArgs a) {
             float tseg = hit >= 0 ? th : INFINITY;
             pd.k = st.k;
             reception(a, r, st, tseg, faces_sh, stride_sh, pd, rxt);
-            if (hit < 0 || st.k == a.max_order) {
+            if (SBR_CHECKED_ON && hit >= 0 && (unsigned)face >= (unsigned)a.scene.nf) {
+                check_fail(a.scene, SBR_CHECK_FACE_ID);
+                alive = false;
+            } else if (hit < 0 || st.k == a.max_order) {
                 alive = false;
             } else {
                 // specular reflection on the hit face's plane (faces_sh[j], j < pd.k, stay

@@ -74,6 +74,17 @@ __device__ __forceinline__ RayPre make_ray(float3 o, float3 d) {
     return r;
 }
 
+// SBR_CHECKED builds: record a failed bounds check (bit = SBR_CHECK_*) in the launch's
+// status word.  The caller then ends the query that failed; nothing traps.
+__device__ __forceinline__ void check_fail(const SceneDev &S, unsigned bit) {
+    if (S.status) atomicOr(S.status, (unsigned long long)bit);
+}
+#ifdef SBR_CHECKED
+#define SBR_CHECKED_ON 1
+#else
+#define SBR_CHECKED_ON 0
+#endif
+
 // Three-input min / max (one instruction each on sm_100 and later).
 __device__ __forceinline__ float max3f(float a, float b, float c) {
     float d;
@@ -186,6 +197,12 @@ __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, 
             float d0 = dist[0], d1 = dist[1], d2 = dist[2], d3 = dist[3];
             float dmin = fminf(min3f(d0, d1, d2), d3);
             if (dmin < INFINITY) {
+                if (SBR_CHECKED_ON && sp + 3 > S.stack_limit) {   // up to three pushes follow
+                    check_fail(S, SBR_CHECK_TRACE_STACK);
+                    t_out = tbest;
+                    face_out = bface;
+                    return -1;
+                }
                 int pick = d0 == dmin ? 0 : (d1 == dmin ? 1 : (d2 == dmin ? 2 : 3));
                 if (d3 < INFINITY && pick != 3) stack[sp++] = refs.w;
                 if (d2 < INFINITY && pick != 2) stack[sp++] = refs.z;
@@ -252,6 +269,10 @@ __device__ __forceinline__ bool any_hit4(const SceneDev &S, const RayPre &r, flo
             const float tnz[4] = {nz01.x, nz01.y, nz23.x, nz23.y}, tfz[4] = {fz01.x, fz01.y, fz23.x, fz23.y};
             const int rf[4] = {refs.x, refs.y, refs.z, refs.w};
             int next = 0x7fffffff;
+            if (SBR_CHECKED_ON && sp + 3 > S.stack_limit) {   // up to three pushes follow
+                check_fail(S, SBR_CHECK_OCCLUSION_STACK);
+                return false;
+            }
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 float tn = max3f(tnx[c], tny[c], fmaxf(tnz[c], tmin));

@@ -10,6 +10,12 @@
 
 #include "../../include/sbr.h"
 
+#ifdef SBR_CHECKED
+#define SBR_CHECKED_BUILD 1
+#else
+#define SBR_CHECKED_BUILD 0
+#endif
+
 namespace sbr {
 
 constexpr int kMaxOrder = SBR_MAX_ORDER;
@@ -23,7 +29,7 @@ constexpr int kStack4 = 96;        // 4-wide traversal stack (the builder checks
 // Device counters of one launch (int64 each).
 enum Counter {
     kRays = 0, kSegments, kNodeVisits, kTriTests, kRxTests, kRecords, kPaths, kCollisions,
-    kRayHead, kBatchHead, kBatchDone, kErrorFlags, kWedgeTests, kDiffRecords, kDiffCand,
+    kRayHead, kBatchHead, kBatchDone, kErrorFlags, kWedgeTests, kDiffRecords, kDiffCand, kNonFinite,
     kNumCounters = 16
 };
 
@@ -72,6 +78,11 @@ struct SceneDev {
     const float4 *wnodes;
     const int *wedge_bvh_ids;
     int nw;
+    // SBR_CHECKED builds: a failed bounds check ORs its SBR_CHECK_* bit into *status (the
+    // running launch's counters[kErrorFlags]; null: not recorded) and the query that failed
+    // stops; traversal walks push at most stack_limit entries (<= their array sizes)
+    unsigned long long *status;
+    int stack_limit;
 };
 
 struct RxDev {
@@ -178,6 +189,7 @@ struct sbr_paths {
     int64_t table_slots = 0;
     long long *counters = nullptr;         // sbr::kNumCounters
     int *pair_off = nullptr;               // per-pair path ranges (sbr_refine_pair), lazily sized
+    std::vector<int> pair_host;            // host copy of the per-pair offsets [npairs + 1]
     int64_t pair_cap = 0;
     void *pair_mem = nullptr;
     size_t pair_bytes = 0;
@@ -189,6 +201,7 @@ struct sbr_paths {
     int32_t ntx = 0, nrx = 0, n_div = 0, max_order = 0, launcher = 0;
     const sbr_rxset *rx = nullptr;
     float alpha = 1.0f;
+    int64_t ray_begin = 0, ray_count = 0;  // ray ids traced per transmitter by the last launch
     bool timed = false;                    // last launch recorded kernel events
     int trace_grid = 0, trace_block = 0;
 };
@@ -235,7 +248,8 @@ struct TraceArgs {
     const float4 *dirs;
     const float4 *tx;
     int ntx;
-    int64_t nrays_per_tx;
+    int64_t nrays_per_tx;     // rays traced per transmitter: ids ray_begin .. ray_begin + nrays_per_tx
+    int64_t ray_begin;
     int max_order;
     float cone;               // reception cone half-angle (rad)
     float tan_cone;
@@ -257,7 +271,8 @@ struct DiffractArgs {
     const float4 *dirs;
     const float4 *tx;
     int ntx;
-    int64_t nrays_per_tx;
+    int64_t nrays_per_tx;     // rays searched per transmitter: ids ray_begin .. ray_begin + nrays_per_tx
+    int64_t ray_begin;
     float cone, tan_cone;
     RecDev *recs;
     int64_t rec_cap;
@@ -276,8 +291,15 @@ struct DedupArgs {
     int64_t path_cap;
     const float4 *dirs;       // lattice directions (rough launch direction)
     long long *counters;
+    int nrx;                  // paths of pair (tx, rx) are emitted iff (tx * nrx + rx) % shard_world
+    int shard_rank, shard_world;   // == shard_rank
 };
 cudaError_t launch_dedup(const DedupArgs &a, int num_sms, cudaStream_t s);
+// counters of a container whose records were replaced: kRecords = n, kPaths = kCollisions = 0
+cudaError_t launch_records_reset(long long *counters, long long n, cudaStream_t s);
+// counters[kNonFinite] = valid paths with a non-finite output
+cudaError_t launch_nonfinite_scan(const sbr_path_record *paths, long long *counters, int64_t path_cap, int num_sms,
+                                  cudaStream_t s);
 
 struct RefineArgs {
     SceneDev scene;

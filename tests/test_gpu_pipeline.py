@@ -8,7 +8,7 @@ import torch
 from paper_2208_10009_gb300 import scenes
 
 from parity_util import (EDGE_MARGIN, TOL_ANGLE_RAD, TOL_DELAY_REL, ang, dir_of, gpu_paths_by_key,
-                         oracle_paths_by_key)
+                         oracle_paths_by_key, replay_refinement)
 
 pytestmark = pytest.mark.gpu
 SQ3 = float(np.sqrt(3.0))
@@ -61,26 +61,25 @@ def test_shoebox_per_ray_trace(gpu_ctx, oracle_mod):
     _close(paths, rxs, scene)
 
 
-def _refine_compare(gpu_ctx, oracle_mod, S, tx, rx, got, n, K, iters, alpha, target=0.0, choice=None):
-    """Compare GPU refined records with the oracle refinement started from the same rough
-    ray.  Returns the number of near-tie divergences."""
-    tl = oracle_mod.theta_launch(n)
-    near_ties = 0
+def _refine_compare(gpu_ctx, oracle_mod, S, tx, rx, got, n, K, iters, alpha, choice, target=0.0):
+    """Compare GPU refined records with the oracle: every logged decision against the
+    oracle's replay (argmin, frame axis, stop), the direction against the oracle's own
+    run where the decisions agree, and the outputs of the GPU's own direction.  Returns
+    the number of paths with a tie decided the other way within rounding."""
+    tl = np.float32(oracle_mod.theta_launch(n))
+    ties = 0
     for i, r in enumerate(got):
         k = int(r["order"])
         faces = tuple(int(f) for f in r["faces"][:k])
         c0 = oracle_mod.lattice_ids(n, [int(r["ray"])])[0]
-        e0 = oracle_mod.refine(S, tx[r["tx"]], rx[r["rx"]], faces, c0, 1.0, 9, 0)["err"]
-        ref = oracle_mod.refine(S, tx[r["tx"]], rx[r["rx"]], faces, c0, max(tl, e0), K, iters, target)
-        assert int(r["iters"]) == ref["iters"] or target > 0
-        if choice is not None:
-            ch = choice[i, : ref["iters"]]
-            if not np.array_equal(ch, ref["choice"]):
-                near_ties += 1
-                continue
-        assert ang(r["dir"], ref["dir"]) < TOL_ANGLE_RAD, (faces, ang(r["dir"], ref["dir"]))
+        R0 = max(float(tl), float(r["rough_err"]))
+        rep = replay_refinement(oracle_mod, S, tx[r["tx"]], rx[r["rx"]], faces, c0, R0, K, r, choice[i], iters,
+                                target)
+        ties += rep["ties"] + rep["axis_ties"] > 0
+        ref = oracle_mod.refine(S, tx[r["tx"]], rx[r["rx"]], faces, c0, R0, K, iters, target)
+        if ref["iters"] == int(r["iters"]) and np.array_equal(choice[i, : ref["iters"]] & 15, ref["choice"]):
+            assert ang(r["dir"], ref["dir"]) < TOL_ANGLE_RAD, (faces, ang(r["dir"], ref["dir"]))
         # outputs evaluated on the GPU's own refined direction
-        R0 = max(tl, float(r["rough_err"]))
         bound = oracle_mod.refined_err_bound(R0, K, int(r["iters"])) if r["iters"] > 0 else 0.0
         ev = oracle_mod.path_eval(S, tx[r["tx"]], rx[r["rx"]], faces, r["dir"], err_bound=bound)
         assert bool(r["valid"]) == ev["valid"], faces
@@ -88,7 +87,7 @@ def _refine_compare(gpu_ctx, oracle_mod, S, tx, rx, got, n, K, iters, alpha, tar
         assert ang(dir_of(*r["aod"]), dir_of(*ev["aod"])) < TOL_ANGLE_RAD
         assert ang(dir_of(*r["aoa"]), dir_of(*ev["aoa"])) < TOL_ANGLE_RAD
         assert abs(r["power_dbm"] - ev["power"]) < 1e-3
-    return near_ties
+    return ties
 
 
 def test_shoebox_paths_refine_and_image_method(gpu_ctx, oracle_mod):
@@ -116,8 +115,8 @@ def test_shoebox_paths_refine_and_image_method(gpu_ctx, oracle_mod):
     gpu_ctx.refine(scene, paths, iters, K, choice_log=choice)
     got = gpu_ctx.query(paths)
     ch = choice.cpu().numpy()[: len(got)]
-    near = _refine_compare(gpu_ctx, oracle_mod, S, tx, rx, got, n, K, iters, SQ3, choice=ch)
-    assert near <= 2
+    ties = _refine_compare(gpu_ctx, oracle_mod, S, tx, rx, got, n, K, iters, SQ3, ch)
+    assert ties <= 2
     im = {p["faces"]: p for p in oracle_mod.image_enumerate(S, tx[0], rx[0], order)}
     for r in got:
         key = tuple(int(f) for f in r["faces"][: r["order"]])
@@ -259,16 +258,19 @@ def test_nonconvex_face_validity(gpu_ctx, oracle_mod):
 def test_batched_and_per_pair_equal_plain(gpu_ctx, oracle_mod):
     """a9: the persistent work-queue form and the per-pair form give the plain form's
     results (same device arithmetic, different schedule).  With the early stop at 0.01 deg
-    (§III.B) the iteration counts match the oracle's (argmin near-ties aside) and every
-    valid path that stopped before the cap has its AOD and AOA within the target of the
-    image-method path."""
+    (§III.B) every decision of every path (argmin, frame axis, stop) agrees with the
+    oracle's replay, and every valid path that stopped before the cap has its AOD and AOA
+    within the target of the image-method path."""
     sc, tx, rx = scenes.office(nbox=60, ntx=2, nrx=12, g_shell=8, g_box=1)
     scene, rxs, paths = _setup(gpu_ctx, sc, tx, rx, 1 << 18, 1 << 16)
     res = []
+    choice = torch.full((paths.path_cap, 8), -1, dtype=torch.int8, device="cuda")
     for mode in ("plain", "batch", "batch8", "batch32", "batch1", "pair"):
         gpu_ctx.launch(scene, tx, rxs, paths, 48, 3, rx_angle_scale=SQ3, sync=True)
         if mode == "plain":
-            gpu_ctx.refine(scene, paths, 8, 16, target=np.radians(0.01))
+            gpu_ctx.refine(scene, paths, 8, 16, target=np.radians(0.01), choice_log=choice)
+            plain_log = {(int(g["tx"]), int(g["rx"]), int(g["order"]), tuple(g["faces"])): row
+                         for g, row in zip(gpu_ctx.query(paths), choice.cpu().numpy())}
         elif mode.startswith("batch"):
             lanes = int(mode[5:] or 16)
             gpu_ctx.batch_refine(scene, paths, 8, 16, target=np.radians(0.01), lanes_per_path=lanes)
@@ -287,19 +289,22 @@ def test_batched_and_per_pair_equal_plain(gpu_ctx, oracle_mod):
             assert ang(g["dir"], h["dir"]) < 1e-9
             assert abs(g["delay"] - h["delay"]) <= 1e-12 * g["delay"]
     S = oracle_mod.Scene.from_generated(sc)
-    tl, target = oracle_mod.theta_launch(48), np.radians(0.01)
-    near = early = 0
-    for (t, r, k, fs), g in res[0].items():
+    tl, target = np.float32(oracle_mod.theta_launch(48)), np.radians(0.01)
+    ties = early = 0
+    for key, g in res[0].items():
+        t, r, k, fs = key
         faces = fs[:k]
         c0 = oracle_mod.lattice_ids(48, [int(g["ray"])])[0]
-        ref = oracle_mod.refine(S, tx[t], rx[r], faces, c0, max(tl, float(g["rough_err"])), 16, 8, target)
-        near += int(g["iters"]) != ref["iters"]
+        # every decision, the early stop at the target included, against the oracle's replay
+        rep = replay_refinement(oracle_mod, S, tx[t], rx[r], faces, c0, max(float(tl), float(g["rough_err"])), 16, g,
+                                plain_log[key], 8, target)
+        ties += rep["ties"] + rep["axis_ties"] > 0
         if g["valid"] and g["iters"] < 8:
             im = oracle_mod.image_path(S, tx[t], rx[r], faces)
             assert ang(g["dir"], im["aod_dir"]) <= target * (1 + 1e-3) + 1e-6
             assert ang(dir_of(*g["aoa"]), dir_of(*im["aoa"])) <= target * (1 + 1e-3) + 1e-6
             early += 1
-    assert near <= 0.05 * len(res[0]) and early > 30
+    assert ties <= 0.05 * len(res[0]) and early > 30
     _close(paths, rxs, scene)
 
 

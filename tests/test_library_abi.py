@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(lib):
 
 def test_host_functions(lib):
     from paper_2208_10009_gb300 import api
-    assert lib.sbr_abi_version() == 2
+    assert lib.sbr_abi_version() == 3
     assert lib.sbr_status_string(0) == b"ok"
     for n in (1, 2, 21, 64, 700, 2200):
         assert api.num_rays(n) == 10 * n * n + 2

@@ -99,6 +99,9 @@ def test_early_stop_at_target(oracle_mod, shoebox_run):
         assert r["iters"] < 12
         aod, aoa = errors(p, r["dir"])
         assert abs(aod - r["err"]) < 1e-12 and aod <= target and aoa <= target * (1 + 1e-9)
+        # the stop test's own pair of errors equals the image-method comparison
+        pe = oracle_mod.path_errors(S, tx[0], rx[0], p["faces"], r["dir"])
+        assert abs(pe[0] - aod) < 1e-12 and abs(pe[1] - aoa) < 1e-11
         if r["iters"] > 0:
             q = oracle_mod.refine(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 9, r["iters"] - 1, target)
             assert np.array_equal(q["choice"], r["choice"][:-1])
@@ -201,16 +204,22 @@ def test_replay_hooks(oracle_mod, shoebox_run):
         assert np.array_equal(a["choice"], b["choice"]) and a["iters"] == b["iters"] == 6
         assert np.array_equal(np.argmin(b["sub_err"], axis=1), b["choice"])
         assert np.array_equal(b["sub_err"].min(axis=1), b["err_hist"][1:])
-        c = oracle_mod.refine_ex(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 9, 6, forced=b["choice"])
+        own = b["choice"] | (b["axis"] << 4)
+        c = oracle_mod.refine_ex(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 9, 6, forced=own)
         assert np.array_equal(c["dir"], b["dir"]) and np.array_equal(c["sub_err"], b["sub_err"])
-        f = b["choice"].copy()
-        f[2] = (f[2] + 1) % 9
+        # another frame axis at iteration 1 rotates that iteration's sub-rays about the centre
+        g = own.copy()
+        g[1] = (g[1] & 15) | (((b["axis"][1] + 1) % 3) << 4)
+        h = oracle_mod.refine_ex(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 9, 6, forced=g, stall=False)
+        assert np.array_equal(h["sub_err"][0], b["sub_err"][0]) and not np.array_equal(h["sub_err"][1], b["sub_err"][1])
+        f = own.copy()
+        f[2] = (f[2] & 0x30) | (((f[2] & 15) + 1) % 9)
         # a forced second-best choice may leave the exact direction outside later cones:
         # the stalled-path exit is off so that all six forced iterations run
         d = oracle_mod.refine_ex(S, tx[0], rx[0], p["faces"], p["rough_dir"], R0, 9, 6, forced=f, stall=False)
-        assert np.array_equal(d["choice"], f)
+        assert np.array_equal(d["choice"], f & 15)
         assert np.array_equal(d["sub_err"][:3], b["sub_err"][:3])
-        assert d["err_hist"][3] == b["sub_err"][2, f[2]] and not np.array_equal(d["dir"], b["dir"])
+        assert d["err_hist"][3] == b["sub_err"][2, f[2] & 15] and not np.array_equal(d["dir"], b["dir"])
 
 
 def test_convergence_orders_distance_and_power(oracle_mod):

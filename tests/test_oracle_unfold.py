@@ -73,3 +73,25 @@ def test_unfold_gradient_central_differences(oracle_mod, seed):
             scale = np.array([1, 1, 1, 1 / C0, 1e-3, 1e-3, 1e-3, 1e-3]) * max(np.abs(J[:, c]).max(), 1e-12)
             err = np.abs(fd - J[:, c])
             assert np.all(err <= 1e-5 * np.maximum(np.abs(J[:, c]), scale)), (faces, c, fd, J[:, c])
+
+
+def test_unfold_many_equals_unfold(oracle_mod):
+    """The batched form returns the one-path values (az = el = 0) for every path, and its
+    AOD / AOA / delay equal the image method's on the shoebox's 63 paths."""
+    from paper_2208_10009_gb300 import scenes
+    sc, tx, rx = scenes.shoebox_config()
+    S = oracle_mod.Scene.from_generated(sc)
+    im = oracle_mod.image_enumerate(S, tx[0], rx[0], 3)
+    assert len(im) == 63
+    order = np.array([len(p["faces"]) for p in im])
+    faces = np.full((len(im), 8), -1)
+    for i, p in enumerate(im):
+        faces[i, : order[i]] = p["faces"]
+    T, R = np.repeat(tx, len(im), 0), np.repeat(rx, len(im), 0)
+    v = oracle_mod.unfold_many(S, order, faces, T, R)
+    for i, p in enumerate(im):
+        one, _ = oracle_mod.unfold(S, p["faces"], tx[0], rx[0], 0.0, 0.0)
+        assert np.array_equal(v[i], one)
+        d = np.array([np.cos(v[i, 5]) * np.cos(v[i, 4]), np.cos(v[i, 5]) * np.sin(v[i, 4]), np.sin(v[i, 5])])
+        assert np.arctan2(np.linalg.norm(np.cross(d, p["aod_dir"])), d @ p["aod_dir"]) < 1e-12
+        assert abs(v[i, 3] / p["delay"] - 1) < 1e-13
