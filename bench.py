@@ -96,6 +96,43 @@ def recorded_traffic(path, sources):
     return rec["dram_bytes_per_launch"], rec
 
 
+def fp32_peak(device: int):
+    """The FP32 FMA rate of this GPU from the microbenchmark library (scalar fma.rn.f32 and
+    packed fma.rn.f32x2, best of three launches each); None if it is not built."""
+    import ctypes
+
+    from paper_2208_10009_gb300 import build as _b
+    if not os.path.exists(_b.SO_PROBE):
+        return None
+    lib = ctypes.CDLL(_b.SO_PROBE)
+    lib.sbr_probe_fp32.restype = ctypes.c_int
+    lib.sbr_probe_fp32.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
+    best = {}
+    for packed in (0, 1):
+        r = []
+        for _ in range(3):
+            f, ms = ctypes.c_double(), ctypes.c_float()
+            if lib.sbr_probe_fp32(device, packed, 8, 200000, ctypes.byref(f), ctypes.byref(ms)) != 0:
+                return None
+            r.append(f.value / 1e12)
+        best[packed] = max(r)
+    form = "packed fma.rn.f32x2" if best[1] > best[0] else "scalar fma.rn.f32"
+    return {"tflops": max(best.values()), "scalar_tflops": best[0], "packed_tflops": best[1], "form": form}
+
+
+def recorded_issue(workload):
+    """Issue-slot utilisation (sm__issue_active) of the trace kernel from the committed ncu
+    record of this workload, while the kernel sources are unchanged since the capture."""
+    path = TRAFFIC_FILES.get(workload)
+    if not path:
+        return None, None
+    val, rec = recorded_traffic(path, TRACE_SOURCES)
+    if val is None or rec is None or "issue_active_pct" not in rec:
+        return None, rec
+    return rec["issue_active_pct"], rec
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -393,8 +430,11 @@ def run_gpu(args):
     flops = FLOP_NODE * st_t["node_visits"] + FLOP_TRI * st_t["tri_tests"] + FLOP_RX * st_t["rx_tests"]
     peaks, src = _peaks()
     sms = ctx.num_sms
-    peak_tflops = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    derived_tflops = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    probe = fp32_peak(local)
+    peak_tflops = probe["tflops"] if probe else derived_tflops
     achieved = flops / (st_t["ms_trace"] / 1e3) / 1e12
+    issue, issue_rec = recorded_issue(args.workload)
     traffic, traffic_rec = (recorded_traffic(TRAFFIC_FILES[args.workload], TRACE_SOURCES)
                             if args.workload in TRAFFIC_FILES and world == 1 else (None, None))
 
@@ -426,8 +466,12 @@ def run_gpu(args):
            "roofline": {"bound": "alu", "kernel": "trace_kernel", "achieved": achieved, "peak": peak_tflops,
                         "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                         "traffic_source": None if traffic is None else traffic_rec.get("capture"),
-                        "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} MEASURED_PEAKS.json)",
-                        "flops_per_launch": flops, "trace_ms": st_t["ms_trace"]},
+                        "peak_source": ("measured: FP32 FMA microbenchmark in this run (" + probe["form"] + "), "
+                                        f"{probe['scalar_tflops']:.1f} TF/s scalar, {probe['packed_tflops']:.1f} packed"
+                                        if probe else f"derived: {sms} SMs x 128 FP32 lanes x 2 x sm_max_mhz ({src} "
+                                        "MEASURED_PEAKS.json)"),
+                        "derived_peak": derived_tflops, "flops_per_launch": flops, "trace_ms": st_t["ms_trace"],
+                        "issue_active": issue, "issue_source": None if issue is None else issue_rec.get("capture")},
            "clocks": clocks, "gpu_launches": _launches_per_step(opts, world) * args.steps,
            "wall_s": t_wall, "e2e": e2e}
     if rank == 0 and not args.no_cpu_baseline:

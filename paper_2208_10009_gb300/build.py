@@ -5,7 +5,8 @@ statically.  The output lives in ``paper_2208_10009_gb300/_lib/`` (git-ignored) 
 rebuilt when any source or header is newer than it.  A second variant,
 ``libsbr_checked.so``, is compiled with -DSBR_CHECKED: device bounds checks on traversal
 stacks and face ids that report through the launch's status word (SBR_ECHECK) instead of
-faulting.
+faulting.  ``libsbr_probe.so`` holds the FP32 FMA microbenchmark the benchmark's roofline
+divides by (a measurement utility; the SBR library does not link it).
 """
 from __future__ import annotations
 
@@ -21,10 +22,12 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 SO = os.path.join(OUT, "libsbr.so")
 SO_CHECKED = os.path.join(OUT, "libsbr_checked.so")
+SO_PROBE = os.path.join(OUT, "libsbr_probe.so")   # FP32 peak microbenchmark (measurement only)
 SOURCES = ["capi.cu", "host_geometry.cpp", "host_wedges.cpp", "host_faces.cpp", "kernels_trace.cu", "kernels_diffract.cu",
            "kernels_paths.cu", "kernels_refine.cu", "kernels_unfold.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-VARIANTS = {SO: [], SO_CHECKED: ["-DSBR_CHECKED"]}
+VARIANTS = {SO: [], SO_CHECKED: ["-DSBR_CHECKED"], SO_PROBE: []}
+VARIANT_SOURCES = {SO: SOURCES, SO_CHECKED: SOURCES, SO_PROBE: ["probe_fp32.cu"]}
 
 
 def nvcc() -> str:
@@ -58,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, checked: bool = True) -> s
 
     def compile_one(job):
         so, src = job
-        sub = os.path.join(OUT, "checked") if so == SO_CHECKED else OUT
+        sub = {SO_CHECKED: os.path.join(OUT, "checked"), SO_PROBE: os.path.join(OUT, "probe")}.get(so, OUT)
         os.makedirs(sub, exist_ok=True)
         obj = os.path.join(sub, os.path.splitext(src)[0] + ".o")
         cmd = [cc] + _flags() + VARIANTS[so] + (["-x", "cu"] if src.endswith(".cpp") else []) + \
@@ -70,7 +73,7 @@ def build(force: bool = False, verbose: bool = False, checked: bool = True) -> s
             print(r.stdout, r.stderr)
         return so, obj
 
-    jobs = [(so, src) for so in todo for src in SOURCES]
+    jobs = [(so, src) for so in todo for src in VARIANT_SOURCES[so]]
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), max(os.cpu_count() or 4, 4))) as ex:
         done = list(ex.map(compile_one, jobs))
     for so in todo:
