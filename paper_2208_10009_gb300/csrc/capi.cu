@@ -423,8 +423,19 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     if (wids.empty()) wids.push_back(0);
     std::vector<float4> pl4((size_t)std::max(nf, 1));
     std::vector<float> eps((size_t)std::max(nf, 1), 0.0f);
+    // the FP64 planes also as float pairs hi + lo (lo = the rounding residual), per face
+    // (hi, lo): the compensated-FP32 unfolding of the refinement starts from them
+    std::vector<float4> pldf(2 * pl4.size(), make_float4(0, 0, 0, 0));
+    auto split = [](double x, float &hi, float &lo) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+    };
     for (int f = 0; f < nf; ++f) {
         pl4[f] = make_float4((float)planes[f].x, (float)planes[f].y, (float)planes[f].z, (float)planes[f].w);
+        split(planes[f].x, pldf[2 * f].x, pldf[2 * f + 1].x);
+        split(planes[f].y, pldf[2 * f].y, pldf[2 * f + 1].y);
+        split(planes[f].z, pldf[2 * f].z, pldf[2 * f + 1].z);
+        split(planes[f].w, pldf[2 * f].w, pldf[2 * f + 1].w);
         if (face_eps) eps[f] = face_eps[f];
     }
     std::vector<int2> outline;
@@ -434,7 +445,7 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     if (!sc) return fail(ctx, SBR_ENOMEM, "scene: host allocation failed");
     int2 *d_ol;
     float4 *d_olv;
-    float4 *d_nodes, *d_nodes4, *d_tris, *d_pl;
+    float4 *d_nodes, *d_nodes4, *d_tris, *d_pl, *d_pldf;
     Plane64 *d_pld;
     float *d_eps;
     int *d_off, *d_idx, *d_wid;
@@ -445,6 +456,7 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     cv.add(&d_tris, tri4.size());
     cv.add(&d_pl, pl4.size());
     cv.add(&d_pld, planes.size());
+    cv.add(&d_pldf, pldf.size());
     cv.add(&d_eps, eps.size());
     cv.add(&d_off, off.size());
     cv.add(&d_idx, std::max<size_t>(idx.size(), 1));
@@ -466,6 +478,7 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     if (nt) SBR_CUDA(cudaMemcpyAsync(d_tris, tri4.data(), tri4.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_pl, pl4.data(), pl4.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_pld, planes.data(), planes.size() * sizeof(Plane64), cudaMemcpyHostToDevice, s));
+    SBR_CUDA(cudaMemcpyAsync(d_pldf, pldf.data(), pldf.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_eps, eps.data(), eps.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     SBR_CUDA(cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     if (nt) SBR_CUDA(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -480,6 +493,7 @@ sbr_status sbr_scene_upload(sbr_ctx *ctx, const float *verts, int64_t nv, const 
     sc->dev.tris = d_tris;
     sc->dev.planes = d_pl;
     sc->dev.planes_d = d_pld;
+    sc->dev.planes_df = d_pldf;
     sc->dev.face_eps = d_eps;
     sc->dev.face_tri_off = d_off;
     sc->dev.face_tri_idx = d_idx;

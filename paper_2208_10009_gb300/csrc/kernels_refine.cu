@@ -10,6 +10,7 @@
 // traces each through the path's fixed face planes, evaluates Eq. 3 at Rx, keeps the
 // smallest (lowest k on ties) and shrinks R by the pattern's factor.  Iterations run in
 // FP32 while R >= fp64_below and in FP64 after that.
+#include "dfloat.cuh"
 #include "nvtx_ranges.h"
 #include "sbr_device.cuh"
 
@@ -170,15 +171,61 @@ __device__ __forceinline__ D4 unfold_rx(const SceneDev &S, const PathGeo &g) {
     return {x.x, x.y, x.z, 0.0};
 }
 
-__device__ __forceinline__ void set_unf(UnfD &ud, UnfF &uf, int j, const D4 &P) {
-    D4 &dst = j < kMaxOrder ? ud.p[j] : ud.w;
-    dst = P;
-    (j < kMaxOrder ? uf.p[j] : uf.w) = make_float4((float)P.x, (float)P.y, (float)P.z, (float)P.w);
+// The FP32 copies the FP32 iterations use: the same mirror chains in compensated FP32
+// pairs (dfloat.cuh, about 44 bits) from the per-face pairs of the FP64 planes, rounded
+// once to FP32 -- the value the FP64 chain rounds to, except within 2^-44 of a rounding
+// boundary -- without GB300's 1/64-rate FP64 pipe.
+__device__ __forceinline__ void plane_df(const SceneDev &S, int f, df3 &n, df &h) {
+    const float4 a = __ldg(S.planes_df + 2 * f), b = __ldg(S.planes_df + 2 * f + 1);
+    n = {{a.x, b.x}, {a.y, b.y}, {a.z, b.z}};
+    h = {a.w, b.w};
+}
+
+__device__ __forceinline__ float df_round(df x) { return __fadd_rn(x.hi, x.lo); }
+__device__ __forceinline__ float3 df3_round(const df3 &a) { return make_float3(df_round(a.x), df_round(a.y), df_round(a.z)); }
+__device__ __forceinline__ dvec3 df3_double(const df3 &a) { return dv(df_to_double(a.x), df_to_double(a.y), df_to_double(a.z)); }
+
+__device__ __noinline__ float4 unfold_plane32(const SceneDev &S, const PathGeo &g, int j) {
+    df3 n;
+    df h;
+    plane_df(S, g.faces[j], n, h);
+    for (int m = j - 1; m >= 0; --m) {
+        df3 q;
+        df qh;
+        plane_df(S, g.faces[m], q, qh);
+        const df nm2 = df_scale2(df_dot(n, q), 2.0f);
+        n = df3_sub_scaled(n, nm2, q);
+        h = df_sub(h, df_mul(nm2, qh));
+    }
+    const df3 t = {df_of(g.tx.x), df_of(g.tx.y), df_of(g.tx.z)};
+    const df num = df_sub(h, df_dot(n, t));
+    return make_float4(df_round(n.x), df_round(n.y), df_round(n.z), df_round(num));
+}
+
+__device__ __noinline__ float4 unfold_rx32(const SceneDev &S, const PathGeo &g) {
+    if (g.wedge >= 0) {
+        const dvec3 W = wedge_unfold(S, g.wedge, g.txd, g.rxd);
+        return make_float4((float)W.x, (float)W.y, (float)W.z, 0.0f);
+    }
+    df3 x = {df_of(g.rx.x), df_of(g.rx.y), df_of(g.rx.z)};
+    for (int m = g.k - 1; m >= 0; --m) {
+        df3 q;
+        df qh;
+        plane_df(S, g.faces[m], q, qh);
+        const df s2 = df_scale2(df_sub(df_dot(q, x), qh), 2.0f);
+        x = df3_sub_scaled(x, s2, q);
+    }
+    return make_float4(df_round(df_sub(x.x, df_of(g.tx.x))), df_round(df_sub(x.y, df_of(g.tx.y))),
+                       df_round(df_sub(x.z, df_of(g.tx.z))), 0.0f);
 }
 
 __device__ __forceinline__ void build_unf(const SceneDev &S, const PathGeo &g, UnfD &ud, UnfF &uf) {
-    for (int j = 0; j < g.k; ++j) set_unf(ud, uf, j, unfold_plane(S, g, j));
-    set_unf(ud, uf, kMaxOrder, unfold_rx(S, g));
+    for (int j = 0; j < g.k; ++j) {
+        ud.p[j] = unfold_plane(S, g, j);
+        uf.p[j] = unfold_plane32(S, g, j);
+    }
+    ud.w = unfold_rx(S, g);
+    uf.w = unfold_rx32(S, g);
 }
 
 // |d x W|^2 of sub-ray d (+inf if invalid); dw = d . W
@@ -448,9 +495,9 @@ __device__ __forceinline__ int iterate64(const UnfD &ud, int nk, int K, int off,
 // p lies in (or on the boundary of) face f's convex outline: every edge function
 // cross(b - a, p - a) . n of the counter-clockwise corners is >= 0.  FP32 with the
 // triangle test's rounding band below; a sign inside the band is decided in FP64.
-__device__ __noinline__ bool point_in_outline(const SceneDev &S, int f, int2 ol, dvec3 p) {
+__device__ __noinline__ bool point_in_outline(const SceneDev &S, int f, int2 ol, const df3 &pd) {
     const float3 nf = f3(__ldg(S.planes + f));
-    const float3 P = make_float3((float)p.x, (float)p.y, (float)p.z);
+    const float3 P = df3_round(pd);
     const float pn = fabsf(P.x) + fabsf(P.y) + fabsf(P.z) + 1.0f;
     const float4 *cv = S.outline_v + ol.x;
     bool unsure = false;
@@ -467,6 +514,7 @@ __device__ __noinline__ bool point_in_outline(const SceneDev &S, int f, int2 ol,
         a = b;
     }
     if (!unsure) return true;
+    const dvec3 p = df3_double(pd);
     const Plane64 pl = S.planes_d[f];
     const dvec3 n = dv(pl.x, pl.y, pl.z);
     float4 a4 = __ldg(cv + ol.y - 1);
@@ -480,11 +528,12 @@ __device__ __noinline__ bool point_in_outline(const SceneDev &S, int f, int2 ol,
     return true;
 }
 
-__device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p) {
+__device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, const df3 &pd) {
     const int2 ol = __ldg(S.face_outline + f);
-    if (ol.y > 0) return point_in_outline(S, f, ol, p);
+    if (ol.y > 0) return point_in_outline(S, f, ol, pd);
     const float3 nf = f3(__ldg(S.planes + f));   // the FP64 normal rounded to FP32
-    const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
+    const float3 Pf = df3_round(pd);
+    const float px = Pf.x, py = Pf.y, pz = Pf.z;
     const float tol = 1e-6f * (fabsf(px) + fabsf(py) + fabsf(pz)) + 1e-6f;
     int stack[kStackDepth];
     int sp = 0;
@@ -540,6 +589,7 @@ __device__ __forceinline__ bool point_in_face(const SceneDev &S, int f, dvec3 p)
                 if (sa && sb && sc) return true;
                 const Plane64 pl = S.planes_d[f];
                 const dvec3 n = dv(pl.x, pl.y, pl.z);
+                const dvec3 p = df3_double(pd);
                 dvec3 a = dv(A.x, A.y, A.z), b = dv(B.x, B.y, B.z), c = dv(C.x, C.y, C.z);
                 double da = ddot(dcross(b - a, p - a), n);
                 double db = ddot(dcross(c - b, p - b), n);
@@ -566,49 +616,77 @@ __device__ __forceinline__ void az_el(dvec3 v, float *out) {
     out[1] = atan2f(z, sqrtf(x * x + y * y));
 }
 
-// Bounce points p_j of launch direction c through the path's fixed planes (FP64), with
-// den_j = n_j . d_j (the incidence cosine up to sign), the direction of the last leg and
-// the sum of the segment parameters t_j (each leg is t_j d_j with |d_j| = |c|: mirroring
-// keeps the length).  Returns false if a segment length is not positive.
-__device__ __forceinline__ bool trace_bounces(const SceneDev &S, const PathGeo &g, dvec3 c, dvec3 *pts,
-                                              double *dens, dvec3 &d_last, double &tsum) {
-    dvec3 o = g.txd, d = c;
-    tsum = 0.0;
-#pragma unroll
-    for (int j = 0; j < kMaxOrder; ++j) {
-        if (j >= g.k) break;
-        Plane64 pl = S.planes_d[g.faces[j]];
-        dvec3 n = dv(pl.x, pl.y, pl.z);
-        double den = ddot(n, d);
-        double t = den != 0.0 ? (pl.w - ddot(n, o)) / den : -1.0;
-        if (!(t > 0.0)) return false;
-        tsum += t;
-        o = o + d * t;
-        pts[j] = o;
-        dens[j] = den;
-        d = d - n * (2.0 * den);
+// The refined ray's walk through the path's fixed planes for the validity test and the
+// outputs, in compensated FP32 pairs (dfloat.cuh, about 44 bits): bounce point o_j, den_j =
+// n_j . d_j (the incidence cosine up to sign), leg direction d_j and the sum of the segment
+// parameters t_j (each leg is t_j d_j with |d_j| = |c|: mirroring keeps the length).  The
+// per-thread and group forms repeat the walk as they need its points (the arithmetic is
+// deterministic, so every repetition gives the same points), which keeps the points out
+// of local memory and the walk off GB300's 1/64-rate FP64 pipe.
+struct BounceWalk {
+    df3 o, d;
+    df tsum;
+    __device__ __forceinline__ void start(const PathGeo &g, dvec3 c) {
+        o = df3_of(g.tx);
+        d = {df_from_double(c.x), df_from_double(c.y), df_from_double(c.z)};
+        tsum = df_of(0.0f);
     }
-    d_last = d;
+    // the bounce on face f; false if the segment length is not positive
+    __device__ __forceinline__ bool step(const SceneDev &S, int f, df &den) {
+        df3 n;
+        df h;
+        plane_df(S, f, n, h);
+        den = df_dot(n, d);
+        if (den.hi == 0.0f) return false;
+        const df t = df_div(df_sub(h, df_dot(n, o)), den);
+        if (!(t.hi > 0.0f)) return false;
+        tsum = df_add(tsum, t);
+        o = df3_add_scaled(o, t, d);
+        d = df3_sub_scaled(d, df_scale2(den, 2.0f), n);
+        return true;
+    }
+};
+
+// First pass of the validity test and the outputs: the whole walk.  Returns false (trace
+// failure) if a segment length is not positive; else the last bounce point (Tx for LOS),
+// the last leg's direction, sum t_j and the Fresnel reflection loss (dB, FP32).
+__device__ __forceinline__ bool walk_path(const RefineArgs &A, const PathGeo &g, dvec3 c, df3 &last, df3 &d_last,
+                                          df &tsum, float &gain_db) {
+    BounceWalk w;
+    w.start(g, c);
+    gain_db = 0.0f;
+    for (int j = 0; j < g.k; ++j) {
+        df den;
+        if (!w.step(A.scene, g.faces[j], den)) return false;
+        const float eps = __ldg(A.scene.face_eps + g.faces[j]);
+        if (eps > 0.0f) gain_db += 20.0f * log10f(fresnel_perp_abs(fabsf(df_round(den)), eps));
+    }
+    last = w.o;
+    d_last = w.d;
+    tsum = w.tsum;
     return true;
 }
 
-// a8 outputs of a traced path: delay = polyline length (FP64) / c0, the legs up to the
-// last bounce point as |c| sum t_j, the last one to Rx from its end points; AOD, AOA and
-// power = ptx + free-space loss + Fresnel reflection losses in FP32, as the record stores
-// them
-__device__ __forceinline__ void path_outputs(const RefineArgs &A, const PathGeo &g, dvec3 c, const dvec3 *pts,
-                                             const double *dens, double tsum, sbr_path_record &p) {
-    const double len = (g.k > 0 ? tsum * dnorm(c) : 0.0) + dnorm(g.rxd - (g.k > 0 ? pts[g.k - 1] : g.txd));
-    float gain_db = 0.0f;
-    for (int j = 0; j < g.k; ++j) {
-        float eps = __ldg(A.scene.face_eps + g.faces[j]);
-        if (eps > 0.0f) gain_db += 20.0f * log10f(fresnel_perp_abs(fabsf((float)dens[j]), eps));
-    }
-    p.delay = len / kC0;
+// Rx is received on the last leg: its foot lies ahead of the last bounce point
+__device__ __forceinline__ bool rx_ahead(const PathGeo &g, const df3 &last, const df3 &d_last) {
+    return df_dot(df3_sub(df3_of(g.rx), last), d_last).hi > 0.0f;
+}
+
+// a8 outputs of a walked path: delay = polyline length / c0 with the legs up to the last
+// bounce point as |c| sum t_j and the last one from its end points; AOD, AOA and power =
+// ptx + free-space loss + Fresnel reflection losses in FP32, as the record stores them
+__device__ __forceinline__ void path_outputs(const RefineArgs &A, const PathGeo &g, dvec3 c, const df3 &last,
+                                             df tsum, float gain_db, sbr_path_record &p) {
+    const df3 cd = {df_from_double(c.x), df_from_double(c.y), df_from_double(c.z)};
+    const df3 v = df3_sub(last, df3_of(g.rx));
+    df len = df_sqrt(df_dot(v, v));
+    if (g.k > 0) len = df_add(len, df_mul(tsum, df_sqrt(df_dot(cd, cd))));
+    const df c0 = {299792448.0f, 10.0f};   // 299792458 m/s as an exact pair
+    p.delay = df_to_double(df_div(len, c0));
     az_el(c, p.aod);
-    az_el((g.k > 0 ? pts[g.k - 1] : g.txd) - g.rxd, p.aoa);
+    az_el(dv(df_round(v.x), df_round(v.y), df_round(v.z)), p.aoa);
     const float lam = (float)(kC0 / A.freq);
-    p.power_dbm = (float)A.ptx_dbm + 20.0f * log10f(lam / (4.0f * 3.14159265f * (float)len)) + gain_db;
+    p.power_dbm = (float)A.ptx_dbm + 20.0f * log10f(lam / (4.0f * 3.14159265f * df_round(len))) + gain_db;
 }
 
 // Upper bound on the final error angle of a refined path whose exact direction lies in
@@ -660,43 +738,45 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
         wedge_finalize(A, g, c, p, err_bound);
         return;
     }
-    dvec3 pts[kMaxOrder];
-    double dens[kMaxOrder];
-    dvec3 dl = c;
-    double tsum;
-    if (!trace_bounces(S, g, c, pts, dens, dl, tsum)) {
+    df3 last, dl;
+    df tsum;
+    float gain_db;
+    if (!walk_path(A, g, c, last, dl, tsum, gain_db)) {
         p.valid = 0;
         p.flags |= SBR_PATH_TRACE_FAIL;
         p.delay = 0.0;
         return;
     }
-    // Rx must be received on the last leg (its foot lies ahead of the last bounce point)
-    // and the refinement must have converged
-    bool valid = ddot(g.rxd - (g.k > 0 ? pts[g.k - 1] : g.txd), dl) > 0.0 && p.err <= err_bound;
-    // The lanes that arrive here together run the queries in lockstep: loop bounds made
-    // uniform over them, a lane that has failed a test idles through the rest, so that the
-    // lanes execute the same traversal code at the same time (a per-lane early exit would
-    // let one lane's occlusion queries run beside another's point-in-face queries).
+    // Rx must be received on the last leg and the refinement must have converged
+    bool valid = rx_ahead(g, last, dl) && p.err <= err_bound;
+    // Second pass: the walk again, each bounce point tested on its face and each leg for
+    // occlusion as it is reached.  The lanes that arrive here together run the queries in
+    // lockstep: loop bounds made uniform over them, a lane that has failed a test idles
+    // through the rest, so that the lanes execute the same traversal code at the same time.
     const unsigned m = __activemask();
     const int kk = __reduce_max_sync(m, g.k);
-    for (int j = 0; j < kk; ++j) {
-        if (!__any_sync(m, valid)) break;
-        if (valid && j < g.k) valid = point_in_face(S, g.faces[j], pts[j]);
-    }
+    BounceWalk w;
+    w.start(g, c);
     for (int j = 0; j <= kk; ++j) {
         if (!__any_sync(m, valid)) break;
         if (!valid || j > g.k) continue;
-        dvec3 from = j == 0 ? g.txd : pts[j - 1];
-        dvec3 to = j == g.k ? g.rxd : pts[j];
-        dvec3 seg = to - from;
-        int fa = j == 0 ? -1 : g.faces[j - 1];
-        int fb = j == g.k ? -1 : g.faces[j];
-        RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
-                            make_float3((float)seg.x, (float)seg.y, (float)seg.z));
+        const df3 from = w.o;
+        df den;
+        if (j < g.k) {
+            w.step(S, g.faces[j], den);   // succeeded in the first pass
+            if (!point_in_face(S, g.faces[j], w.o)) {
+                valid = false;
+                continue;
+            }
+        }
+        const df3 to = j < g.k ? w.o : df3_of(g.rx);
+        const int fa = j == 0 ? -1 : g.faces[j - 1];
+        const int fb = j == g.k ? -1 : g.faces[j];
+        const RayPre r = make_ray(df3_round(from), df3_round(df3_sub(to, from)));
         if (any_hit4(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) valid = false;
     }
     p.valid = valid ? 1 : 0;
-    path_outputs(A, g, c, pts, dens, tsum, p);
+    path_outputs(A, g, c, last, tsum, gain_db, p);
 }
 
 __device__ __forceinline__ void store_result(sbr_path_record *dst, const sbr_path_record &p) {
@@ -930,54 +1010,43 @@ __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
         if (gl == 0) wedge_finalize(A, g, c, p, err_bound);
         return;
     }
-    __syncwarp(gmask);   // every lane has finished reading the unfolded planes
-    if (gl == 0) {
-        dvec3 pts[kMaxOrder];
-        double dens[kMaxOrder];
-        dvec3 dl = c;
-        double tsum;
-        bool ok = trace_bounces(S, g, c, pts, dens, dl, tsum);
-        for (int j = 0; j < g.k; ++j) sh.p[j] = {pts[j].x, pts[j].y, pts[j].z, dens[j]};
-        sh.w = {dl.x, dl.y, dl.z, ok ? tsum : -1.0};
-    }
-    __syncwarp(gmask);
-    if (sh.w.w < 0.0) {
+    // every lane walks the path (the same compensated-FP32 arithmetic as the per-thread
+    // form, so the same points); then lane j tests bounce point j on its face and leg j for
+    // occlusion, walking to it again
+    df3 last, dl;
+    df tsum;
+    float gain_db;
+    if (!walk_path(A, g, c, last, dl, tsum, gain_db)) {
         p.valid = 0;
         p.flags |= SBR_PATH_TRACE_FAIL;
         p.delay = 0.0;
         return;
     }
-    const dvec3 last = g.k > 0 ? dv(sh.p[g.k - 1].x, sh.p[g.k - 1].y, sh.p[g.k - 1].z) : g.txd;
-    // Rx must be received on the last leg (its foot lies ahead of the last bounce point)
-    // and the refinement must have converged
-    bool mine_ok = ddot(g.rxd - last, dv(sh.w.x, sh.w.y, sh.w.z)) > 0.0 && p.err <= err_bound;
-    for (int j = gl; j < g.k && mine_ok; j += G)
-        mine_ok = point_in_face(S, g.faces[j], dv(sh.p[j].x, sh.p[j].y, sh.p[j].z));
-    bool valid = __all_sync(gmask, mine_ok);
-    mine_ok = true;
+    // Rx must be received on the last leg and the refinement must have converged
+    bool valid = rx_ahead(g, last, dl) && p.err <= err_bound;
+    bool mine_ok = true;
     if (valid) {
         for (int j = gl; j <= g.k && mine_ok; j += G) {
-            dvec3 from = j == 0 ? g.txd : dv(sh.p[j - 1].x, sh.p[j - 1].y, sh.p[j - 1].z);
-            dvec3 to = j == g.k ? g.rxd : dv(sh.p[j].x, sh.p[j].y, sh.p[j].z);
-            dvec3 seg = to - from;
-            int fa = j == 0 ? -1 : g.faces[j - 1];
-            int fb = j == g.k ? -1 : g.faces[j];
-            RayPre r = make_ray(make_float3((float)from.x, (float)from.y, (float)from.z),
-                                make_float3((float)seg.x, (float)seg.y, (float)seg.z));
+            BounceWalk w;
+            w.start(g, c);
+            df den;
+            for (int i = 0; i < j; ++i) w.step(S, g.faces[i], den);
+            const df3 from = w.o;
+            if (j < g.k) {
+                w.step(S, g.faces[j], den);
+                mine_ok = point_in_face(S, g.faces[j], w.o);
+                if (!mine_ok) break;
+            }
+            const df3 to = j < g.k ? w.o : df3_of(g.rx);
+            const int fa = j == 0 ? -1 : g.faces[j - 1];
+            const int fb = j == g.k ? -1 : g.faces[j];
+            const RayPre r = make_ray(df3_round(from), df3_round(df3_sub(to, from)));
             if (any_hit4(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) mine_ok = false;
         }
         valid = __all_sync(gmask, mine_ok);
     }
     p.valid = valid ? 1 : 0;
-    if (gl == 0) {
-        dvec3 pts[kMaxOrder];
-        double dens[kMaxOrder];
-        for (int j = 0; j < g.k; ++j) {
-            pts[j] = dv(sh.p[j].x, sh.p[j].y, sh.p[j].z);
-            dens[j] = sh.p[j].w;
-        }
-        path_outputs(A, g, c, pts, dens, sh.w.w, p);
-    }
+    if (gl == 0) path_outputs(A, g, c, last, tsum, gain_db, p);
 }
 
 // At most 85 registers a thread, so that three 256-thread blocks fit on an SM (measured
@@ -1040,8 +1109,14 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
                 if (j < g.k || j == kMaxOrder) (j < kMaxOrder ? uf.p[j] : uf.w) = A.unf[kUnfStride * pi + j];
             cf = f3(A.unf[kUnfStride * pi + kMaxOrder + 1]);
         } else {
-            for (int j = gl; j < g.k; j += G) set_unf(ud, uf, j, unfold_plane(A.scene, g, j));
-            if (gl == G - 1) set_unf(ud, uf, kMaxOrder, unfold_rx(A.scene, g));
+            for (int j = gl; j < g.k; j += G) {
+                ud.p[j] = unfold_plane(A.scene, g, j);
+                uf.p[j] = unfold_plane32(A.scene, g, j);
+            }
+            if (gl == G - 1) {
+                ud.w = unfold_rx(A.scene, g);
+                uf.w = unfold_rx32(A.scene, g);
+            }
             cf = make_float3((float)p.dir[0], (float)p.dir[1], (float)p.dir[2]);
         }
         __syncwarp(gmask);
@@ -1239,12 +1314,8 @@ __global__ void __launch_bounds__(128) batch_unfold_kernel(RefineArgs A) {
         load_path(A, p, g);
         atomicAdd(&hist[order_group(g)], 1u);
         float4 *u = A.unf + kUnfStride * pi;
-        for (int j = 0; j < g.k; ++j) {
-            const D4 P = unfold_plane(A.scene, g, j);
-            u[j] = make_float4((float)P.x, (float)P.y, (float)P.z, (float)P.w);
-        }
-        const D4 W = unfold_rx(A.scene, g);
-        u[kMaxOrder] = make_float4((float)W.x, (float)W.y, (float)W.z, (float)W.w);
+        for (int j = 0; j < g.k; ++j) u[j] = unfold_plane32(A.scene, g, j);
+        u[kMaxOrder] = unfold_rx32(A.scene, g);
         u[kMaxOrder + 1] = make_float4((float)p.dir[0], (float)p.dir[1], (float)p.dir[2], 0.0f);
     }
     __syncthreads();
@@ -1252,12 +1323,14 @@ __global__ void __launch_bounds__(128) batch_unfold_kernel(RefineArgs A) {
 }
 
 // a7/a8 of the batched form.  With many paths (>= split_min), one thread per path: every
-// lane of a warp runs the same validity test and FP64 bounce-point trace on its own path,
-// so GB300's narrow FP64 pipe serves 32 paths per instruction.  With few paths, one warp
-// per path with the point-in-face and occlusion queries spread over its lanes (latency).
-// The cone radius after `iters` iterations is recomputed with the same multiplications.
-// The queries are latency-bound: eight blocks per SM (64 registers, some spilled to L1)
-// measured faster than four without spills.
+// lane of a warp runs the same validity test and bounce-point walk on its own path, the
+// paths taken in the lists the iteration kernels grouped by order.  With few paths, one
+// warp per path with the point-in-face and occlusion queries spread over its lanes
+// (latency).  The cone radius after `iters` iterations is recomputed with the same
+// multiplications.  The queries are latency-bound: eight blocks per SM (64 registers,
+// some spilled to L1) measured faster than four, five or six with fewer spills, and
+// faster than the occlusion queries split into a kernel of their own with a thread per
+// (path, leg) (which walks each path again for every leg).
 __global__ void __launch_bounds__(128, 8) batch_finalize_kernel(RefineArgs A) {
     __shared__ UnfD s_sh[4];
     const long long total = path_count(A);

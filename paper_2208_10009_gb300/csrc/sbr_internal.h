@@ -63,6 +63,7 @@ struct SceneDev {
     const float4 *tris;       // 3 per triangle: (v0, face id bits), (v1, 0), (v2, 0)
     const float4 *planes;     // per face: (n, h) with n.x = h on the plane
     const Plane64 *planes_d;  // same in double
+    const float4 *planes_df;  // same as float pairs: 2 per face, (n, h) rounded and the residuals
     const float *face_eps;    // per face relative permittivity (<= 0: perfect reflector)
     const int *face_tri_off;  // CSR over faces -> triangle indices (BVH order)
     const int *face_tri_idx;
