@@ -177,7 +177,7 @@ typedef struct {
     int32_t grid_blocks;     /* persistent trace grid (0 = one wave over all SMs) */
     int32_t block_threads;   /* multiple of 32, at most 128 (0 = 128) */
     int32_t refill_min;      /* a warp takes new rays once this many of its lanes are idle
-                                (1..32; 0 = 16: keeps a warp's rays neighbours in the lattice) */
+                                (1..32; 0 = 24: keeps a warp's rays neighbours in the lattice) */
     int32_t launcher;        /* 0 = equiangular (§II.B), 20 / 8 = equidistant icosahedron /
                                 octahedron (§II.A); ray ids follow that launcher's order */
     int64_t ray_begin;       /* with SBR_LAUNCH_RAY_RANGE: trace only ray ids [ray_begin, ray_end) */

@@ -221,6 +221,17 @@ __device__ __forceinline__ void reception(const TraceArgs &a, const RayPre &r, c
     const float cnx = oix + gx, cny = oiy + gy, cnz = oiz + gz;
     const float cfx = oix - gx, cfy = oiy - gy, cfz = oiz - gz;
     const float tfar = tcap * 1.0000005f + 1e-6f;
+    {
+        // the receivers' bounding box, grown like the node boxes: one slab test before the
+        // walk (most segments, e.g. those rising above every receiver, end here; 2-3 %
+        // of the trace measured on the canyon and the large city)
+        const float nx = r.nx ? R.hi[0] : R.lo[0], fx = r.nx ? R.lo[0] : R.hi[0];
+        const float ny = r.ny ? R.hi[1] : R.lo[1], fy = r.ny ? R.lo[1] : R.hi[1];
+        const float nz = r.nz ? R.hi[2] : R.lo[2], fz = r.nz ? R.lo[2] : R.hi[2];
+        const float tn = max3f(fmaf(nx, r.inv.x, -cnx), fmaf(ny, r.inv.y, -cny), fmaxf(fmaf(nz, r.inv.z, -cnz), 0.0f));
+        const float tf = min3f(fmaf(fx, r.inv.x, -cfx), fmaf(fy, r.inv.y, -cfy), fminf(fmaf(fz, r.inv.z, -cfz), tfar));
+        if (!(tn <= tf * 1.0000005f)) return;
+    }
     int stack[kStack4];
     int sp = 0;
     int node = 0;
