@@ -52,6 +52,10 @@ WORKLOADS = {
                     gen="shoebox_config", n_div=64, max_order=3, alpha=SQ3, iters=8, K=9,
                     target=float(np.radians(0.01)), cpu_stride=1, ref_stride=7, steps=300),
 }
+# the office at a quarter of its pairs (4 Tx x 1024 Rx, ~0.94M paths, the same many-path
+# refinement kernels): the size the per-kernel ncu captures of the refinement run on
+WORKLOADS["office_quarter"] = dict(WORKLOADS["office"], gen_kw={"ntx": 4}, steps=5,
+                                   workload=WORKLOADS["office"]["workload"].replace("16 Tx", "4 Tx"))
 WORKLOADS["canyon_diffraction"] = dict(WORKLOADS["canyon"], diffraction=True,
                                        workload=WORKLOADS["canyon"]["workload"] + ", plus order-1 diffraction")
 DEFAULT_WORKLOAD = "city"
@@ -276,7 +280,7 @@ def run_reference(args):
         return
     from paper_2208_10009_gb300 import scenes
     W = WORKLOADS[args.workload]
-    sc, tx, rx = getattr(scenes, W["gen"])()
+    sc, tx, rx = getattr(scenes, W["gen"])(**W.get("gen_kw", {}))
     stride = W["ref_stride"]
     for w in range(args.warmup):
         cpu_oracle_sample(W, sc, tx, rx, stride, offset=w)
@@ -304,7 +308,7 @@ def run_reference(args):
 
 def _config(W, sc, tx, rx, world):
     n = W["n_div"]
-    return dict({k: v for k, v in W.items() if k not in ("gen", "cpu_stride", "ref_stride", "steps")},
+    return dict({k: v for k, v in W.items() if k not in ("gen", "gen_kw", "cpu_stride", "ref_stride", "steps")},
                 triangles=int(sc.nt), ntx=int(len(tx)), nrx=int(len(rx)), rays=int(len(tx) * (10 * n * n + 2)),
                 l2="flushed (256 MiB write) between timed steps, outside the event-timed region",
                 parallelism=f"ray-range shards x{world} (records all-gathered)" if world > 1 else "single GPU")
@@ -345,7 +349,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     W = WORKLOADS[args.workload]
     opts = {"diffraction": bool(W.get("diffraction", False))}
-    sc, tx, rx = getattr(scenes, W["gen"])()
+    sc, tx, rx = getattr(scenes, W["gen"])(**W.get("gen_kw", {}))
     n, order, alpha, iters, K, target = (W[k] for k in ("n_div", "max_order", "alpha", "iters", "K", "target"))
     n_rays = 10 * n * n + 2
     stream = torch.cuda.Stream(dev)
