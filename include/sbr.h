@@ -412,8 +412,11 @@ sbr_status sbr_unfold_bwd(sbr_ctx *ctx, const sbr_scene *scene, int64_t npaths, 
  *     was launched since);
  *   - all calls share the array; each call clears it first, and calls whose GPU work
  *     overlaps (e.g. on two streams) race and corrupt each other's output;
- *   - the first call on a device looks up the array's device address for that device;
- *     make that first call before any stream capture.
+ *   - the first call on a device looks up the array's device address for that device,
+ *     and every call made while the context's stream is not capturing looks it up again
+ *     (a device reset moves the array); make the first call on a device, and the first
+ *     after a device reset, before any stream capture;
+ *   - SBR_EINVAL if src's records do not live on the context's device.
  * Asynchronous on the context's stream. */
 #define SBR_NOALLOC_MAX_RECORDS 131072
 sbr_status sbr_dedup_noalloc(sbr_ctx *ctx, const sbr_paths *src, sbr_path_record *out, int64_t cap,

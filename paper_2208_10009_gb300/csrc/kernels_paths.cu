@@ -4,49 +4,19 @@
 // keyed by a 64-bit hash of the face sequence with a 64-bit atomicMin on
 // (error-angle bits, ray id); a second pass checks every record against its slot's
 // winner so that a hash collision is detected, never silently merged.
+#include "dedup_keys.cuh"
 #include "sbr_device.cuh"
 
 namespace sbr {
-
-__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
-    x += 0x9E3779B97F4A7C15ULL;
-    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
-    return x ^ (x >> 31);
-}
-
-__device__ __forceinline__ unsigned long long rec_hash(const RecDev &r) {
-    unsigned long long h = mix64(((unsigned long long)(unsigned)r.tx << 40) ^ ((unsigned long long)(unsigned)r.rx << 8) ^
-                                 (unsigned long long)r.order);
-    for (int j = 0; j < r.order; ++j) h = mix64(h ^ (unsigned long long)(unsigned)(r.faces[j] + 1));
-    return h == ~0ULL ? 0x5bd1e995ULL : h;
-}
-
-__device__ __forceinline__ unsigned long long rec_value(const RecDev &r) {
-    // error angles are >= 0, so their IEEE bits order like the values
-    return ((unsigned long long)__float_as_uint(r.err) << 32) | (unsigned)r.ray;
-}
-
-__device__ __forceinline__ bool same_key(const RecDev &a, const RecDev &b) {
-    if (a.tx != b.tx || a.rx != b.rx || a.order != b.order) return false;
-    for (int j = 0; j < a.order; ++j)
-        if (a.faces[j] != b.faces[j]) return false;
-    return true;
-}
 
 __device__ __forceinline__ long long num_records(const DedupArgs &a) {
     long long n = a.counters[kRecords];
     return n < a.rec_cap ? n : a.rec_cap;
 }
 
-// Slots in use for this launch: the smallest power of two >= 2 n (at least 1024, at most
-// the table's), so that a launch with few records clears and probes a small table that
-// stays in L2 (the distinct keys are at most n: load factor <= 1/2).
+// slots in use for this launch (dedup_slots)
 __device__ __forceinline__ unsigned long long used_slots(const DedupArgs &a) {
-    const long long n = num_records(a);
-    long long s = 1024;
-    while (s < 2 * n && s < a.slots) s <<= 1;
-    return (unsigned long long)(s < a.slots ? s : a.slots);
+    return dedup_slots(num_records(a), a.slots);
 }
 
 // keys and values to all-ones (empty / +inf), winners to -1, over the used slots

@@ -15,13 +15,15 @@
 //     parts that must start empty, and calls whose GPU work overlaps (different streams
 //     or devices' contexts racing on the same device) corrupt each other's results;
 //   - the first call on a device looks the array's device address up for that device
-//     (cudaGetSymbolAddress); make that first call before any stream capture.
+//     (cudaGetSymbolAddress), and every call made while its stream is not capturing looks
+//     it up again (so a call after a device reset sees the array's new address); make the
+//     first call on a device, and the first after a device reset, before any stream capture.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
 
-#include "sbr_internal.h"
+#include "dedup_keys.cuh"
 
 namespace {
 
@@ -49,28 +51,28 @@ struct NaArgs {
     int64_t cap;
 };
 
-__device__ __forceinline__ unsigned long long na_mix(unsigned long long x) {
-    x ^= x >> 33;
-    x *= 0xff51afd7ed558ccdULL;
-    x ^= x >> 33;
-    x *= 0xc4ceb9fe1a85ec53ULL;
-    return x ^ (x >> 33);
-}
-
-__device__ __forceinline__ unsigned long long na_key(const sbr::RecDev &r) {
-    unsigned long long h = na_mix(((unsigned long long)(unsigned)r.tx << 32) ^ (unsigned)r.rx);
-    h = na_mix(h ^ ((unsigned long long)r.order << 56));
-    for (int j = 0; j < r.order; ++j) h = na_mix(h + (unsigned long long)(unsigned)r.faces[j] * 0x9E3779B97F4A7C15ULL);
-    return h == ~0ULL ? 1ULL : h;
-}
-
-__device__ __forceinline__ unsigned long long na_value(const sbr::RecDev &r) {
-    return ((unsigned long long)__float_as_uint(r.err) << 32) | (unsigned)r.ray;
-}
-
 __device__ __forceinline__ long long na_count(const NaArgs &a) {
     long long n = *a.rec_count;
     return n < a.rec_cap ? n : a.rec_cap;
+}
+
+// the slots this call uses, from the record count on the device (as the launch's dedup)
+__device__ __forceinline__ unsigned long long na_slots(const NaArgs &a) { return sbr::dedup_slots(na_count(a), kSlots); }
+
+// empty keys, +inf values and no winners over the slots in use, zero counts: the array
+// keeps the last call's contents
+__global__ void na_clear(NaArgs a) {
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(a.scratch + kKeysOff);
+    unsigned long long *vals = reinterpret_cast<unsigned long long *>(a.scratch + kValsOff);
+    int *winner = reinterpret_cast<int *>(a.scratch + kWinOff);
+    const unsigned long long m = na_slots(a);
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < m;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        keys[i] = ~0ULL;
+        vals[i] = ~0ULL;
+        winner[i] = -1;
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 2) reinterpret_cast<long long *>(a.scratch + kCountOff)[threadIdx.x] = 0;
 }
 
 __global__ void na_insert(NaArgs a) {
@@ -78,18 +80,19 @@ __global__ void na_insert(NaArgs a) {
     unsigned long long *vals = reinterpret_cast<unsigned long long *>(a.scratch + kValsOff);
     int *slot_of = reinterpret_cast<int *>(a.scratch + kSlotOff);
     const long long n = na_count(a);
+    const unsigned long long used = na_slots(a), mask = used - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         sbr::RecDev r = a.recs[i];
-        unsigned long long h = na_key(r), s = h & (kSlots - 1);
+        unsigned long long h = sbr::rec_hash(r), s = h & mask;
         slot_of[i] = -1;
-        for (long long probe = 0; probe < kSlots; ++probe) {
+        for (unsigned long long probe = 0; probe < used; ++probe) {
             unsigned long long prev = atomicCAS(keys + s, ~0ULL, h);
             if (prev == ~0ULL || prev == h) {
-                atomicMin(vals + s, na_value(r));
+                atomicMin(vals + s, sbr::rec_value(r));
                 slot_of[i] = (int)s;
                 break;
             }
-            s = (s + 1) & (kSlots - 1);
+            s = (s + 1) & mask;
         }
     }
 }
@@ -104,7 +107,7 @@ __global__ void na_select(NaArgs a) {
         int s = slot_of[i];
         if (s < 0) continue;
         sbr::RecDev r = a.recs[i];
-        if (vals[s] != na_value(r)) continue;
+        if (vals[s] != sbr::rec_value(r)) continue;
         winner[s] = (int)i;
         unsigned long long p = atomicAdd(reinterpret_cast<unsigned long long *>(counts), 1ULL);
         if ((long long)p >= a.cap) continue;
@@ -144,10 +147,7 @@ __global__ void na_verify(NaArgs a) {
             ++bad;
             continue;
         }
-        const sbr::RecDev &x = a.recs[i], &y = a.recs[w];
-        bool same = x.tx == y.tx && x.rx == y.rx && x.order == y.order;
-        for (int j = 0; same && j < x.order; ++j) same = x.faces[j] == y.faces[j];
-        if (!same) ++bad;
+        if (!sbr::same_key(a.recs[i], a.recs[w])) ++bad;
     }
     if (bad) atomicAdd(reinterpret_cast<unsigned long long *>(counts + 1), (unsigned long long)bad);
 }
@@ -176,13 +176,29 @@ extern "C" sbr_status sbr_dedup_noalloc(sbr_ctx *ctx, const sbr_paths *src, sbr_
         return na_fail(ctx, SBR_EINVAL, "sbr_dedup_noalloc: the container holds no launch whose ray directions "
                                         "are still current on this context");
     if (ctx->device < 0 || ctx->device >= 128) return na_fail(ctx, SBR_EINVAL, "sbr_dedup_noalloc: device id");
+    {
+        // the container's records must live on the context's device
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, src->recs) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+            at.device != ctx->device) {
+            cudaGetLastError();
+            return na_fail(ctx, SBR_EINVAL, "sbr_dedup_noalloc: the container does not belong to the context's device");
+        }
+    }
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);
     void *base = nullptr;
     {
+        // looked up again whenever the stream is not capturing: a device reset gives the
+        // array a new address, and a lookup is not made during capture
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            cs = cudaStreamCaptureStatusNone;
+        }
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[ctx->device]) {
+        if (!g_addr[ctx->device] || cs == cudaStreamCaptureStatusNone) {
             cudaError_t e = cudaGetSymbolAddress(&g_addr[ctx->device], g_dedup_scratch);
             if (e != cudaSuccess) {
                 g_addr[ctx->device] = nullptr;
@@ -195,9 +211,7 @@ extern "C" sbr_status sbr_dedup_noalloc(sbr_ctx *ctx, const sbr_paths *src, sbr_
     }
     unsigned char *sc = static_cast<unsigned char *>(base);
     cudaStream_t s = ctx->stream;
-    // empty keys / +inf values / no winners, zero counters: the array keeps the last call's data
-    cudaError_t e = cudaMemsetAsync(sc + kKeysOff, 0xFF, kSlotOff - kKeysOff, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sc + kCountOff, 0, 2 * sizeof(long long), s);
+    cudaError_t e = cudaSuccess;
     NaArgs a;
     a.scratch = sc;
     a.recs = src->recs;
@@ -208,6 +222,7 @@ extern "C" sbr_status sbr_dedup_noalloc(sbr_ctx *ctx, const sbr_paths *src, sbr_
     a.cap = cap;
     int grid = std::max(1, ctx->num_sms * 2);
     if (e == cudaSuccess) {
+        na_clear<<<grid, 256, 0, s>>>(a);
         na_insert<<<grid, 256, 0, s>>>(a);
         na_select<<<grid, 256, 0, s>>>(a);
         na_verify<<<grid, 256, 0, s>>>(a);

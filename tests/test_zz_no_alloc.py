@@ -58,6 +58,29 @@ def test_dedup_noalloc_matches_launch():
             assert np.array_equal(r["dir"], w["dir"])
     assert torch.cuda.memory_allocated() == before
 
+    # a launch with more records (the canyon's ~1.5k: a larger part of the table in use),
+    # right after the shoebox's calls, at the largest accepted record capacity
+    sc2, tx2, rx2 = scenes.urban_canyon()
+    scene2 = ctx.scene_from(sc2)
+    rxs2 = ctx.rx_upload(rx2)
+    paths2 = ctx.paths_create(131072, 1 << 14)
+    ctx.launch(scene2, tx2, rxs2, paths2, 700, 6, rx_angle_scale=float(np.sqrt(3.0)), sync=True)
+    want2 = _by_key(ctx.query(paths2))
+    assert len(want2) > 300
+    out2 = torch.zeros((1 << 14) * 128, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        st = ctx.lib.sbr_dedup_noalloc(ctx.handle, paths2.handle, out2.data_ptr(), 1 << 14, counts.data_ptr())
+        assert st == 0, ctx.lib.sbr_last_error(ctx.handle)
+        torch.cuda.synchronize()
+        n, collisions = (int(v) for v in counts.cpu())
+        assert collisions == 0 and n == len(want2)
+        got = _by_key(out2.cpu().numpy().view(B.PATH_DTYPE)[:n])
+        assert set(got) == set(want2)
+        assert all(int(got[k]["ray"]) == int(w["ray"]) and got[k]["rough_err"] == w["rough_err"]
+                   for k, w in want2.items())
+    for h in (paths2, rxs2, scene2):
+        h.close()
+
     # a container larger than the fixed maximum is refused with a clear message
     big = ctx.paths_create(131072 + 1, 16)
     ctx.launch(scene, tx, rxs, big, 8, 1, rx_angle_scale=float(np.sqrt(3.0)), sync=True)
