@@ -135,15 +135,18 @@ __device__ __forceinline__ float2 fma2s(float ax, float ay, float b, float c) {
     return r;
 }
 
-// Compare-exchange of (distance, ref) pairs: smaller distance first.
-__device__ __forceinline__ void cswap(float &da, int &ra, float &db, int &rb) {
-    bool sw = db < da;
-    float d = sw ? db : da;
-    int r = sw ? rb : ra;
-    db = sw ? da : db;
-    rb = sw ? ra : rb;
-    da = d;
-    ra = r;
+// Pop the next stack entry whose entry distance (sdist, beside the refs in stack) is within
+// tcull (the closest-hit range grown by the slab test's tolerance); false once the stack
+// holds none.
+__device__ __forceinline__ bool pop_near(const int *stack, const float *sdist, int &sp, float tcull, int &node) {
+    while (sp > 0) {
+        --sp;
+        if (sdist[sp] <= tcull) {
+            node = stack[sp];
+            return true;
+        }
+    }
+    return false;
 }
 
 // Closest hit through the 4-wide BVH.  The walk descends inner nodes in an inner loop and
@@ -152,18 +155,22 @@ __device__ __forceinline__ void cswap(float &da, int &ra, float &db, int &rb) {
 // tests of the four child boxes as
 // t = plane * (1/d) - o * (1/d), the near / far planes picked by the ray's direction
 // signs (so no per-axis min/max), two children per packed FMA and three-input min/max;
-// the hit children are sorted by entry distance, the nearest is visited next and the
-// others pushed farthest first.  Closest hit along o + t d over t in (tmin, tmax],
+// the nearest hit child is visited next and the others are pushed with their entry
+// distances; a popped entry whose entry distance already lies beyond the closest hit
+// found since its push is dropped unvisited (the box test it would face against the
+// shrunk range, so nothing it holds can win).  Closest hit along o + t d over t in (tmin, tmax],
 // skipping triangles of face `skip`; ties in t go to the lower face id, then the lower
 // triangle index.  Returns the triangle index (BVH order) or -1; t_out, face_out set on a
 // hit.  nodes_visited counts 4-wide nodes (four box tests each).
 __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, float tmin, float tmax, int skip,
                                             float &t_out, int &face_out, unsigned &nodes_visited,
                                             unsigned &tris_tested) {
-    int stack[kStack4];
+    int stack[kStack4];    // node or leaf refs
+    float sdist[kStack4];  // their entry distances
     int sp = 0;
     int node = 0;
     float tbest = tmax;
+    float tcull = tmax * 1.0000005f;   // entries entering beyond this are dropped at pop
     int best = -1, bface = 0x7fffffff;
     const float oix = r.o.x * r.inv.x, oiy = r.o.y * r.inv.y, oiz = r.o.z * r.inv.z;
     for (;;) {
@@ -204,18 +211,17 @@ __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, 
                     return -1;
                 }
                 int pick = d0 == dmin ? 0 : (d1 == dmin ? 1 : (d2 == dmin ? 2 : 3));
-                if (d3 < INFINITY && pick != 3) stack[sp++] = refs.w;
-                if (d2 < INFINITY && pick != 2) stack[sp++] = refs.z;
-                if (d1 < INFINITY && pick != 1) stack[sp++] = refs.y;
-                if (d0 < INFINITY && pick != 0) stack[sp++] = refs.x;
+                if (d3 < INFINITY && pick != 3) { stack[sp] = refs.w; sdist[sp++] = d3; }
+                if (d2 < INFINITY && pick != 2) { stack[sp] = refs.z; sdist[sp++] = d2; }
+                if (d1 < INFINITY && pick != 1) { stack[sp] = refs.y; sdist[sp++] = d1; }
+                if (d0 < INFINITY && pick != 0) { stack[sp] = refs.x; sdist[sp++] = d0; }
                 node = pick == 0 ? refs.x : (pick == 1 ? refs.y : (pick == 2 ? refs.z : refs.w));
                 continue;
             }
-            if (sp == 0) {
+            if (!pop_near(stack, sdist, sp, tcull, node)) {
                 done = true;
                 break;
             }
-            node = stack[--sp];
         }
         if (done) break;
         {
@@ -234,9 +240,9 @@ __device__ __forceinline__ int closest_hit4(const SceneDev &S, const RayPre &r, 
                     bface = f;
                 }
             }
+            tcull = tbest * 1.0000005f;
         }
-        if (sp == 0) break;
-        node = stack[--sp];
+        if (!pop_near(stack, sdist, sp, tcull, node)) break;
     }
     t_out = tbest;
     face_out = bface;
