@@ -388,7 +388,11 @@ sbr_status sbr_unfold_fwd(sbr_ctx *ctx, const sbr_scene *scene, int64_t npaths, 
                           float *out);
 /* Vector-Jacobian product of sbr_unfold_fwd: given grad_out [P][8], writes grad_tx,
  * grad_rx [P][3] and grad_az_el [P][2] (DEVICE).  Bounce state is recomputed, not read
- * from the forward pass. */
+ * from the forward pass.  A path with a face id outside [0, nf) gets NaN gradients.  When
+ * every input array is 16-byte aligned and there are at least two 256-path tiles per SM,
+ * the kernel stages whole tiles of the inputs in shared memory with bulk copies (same
+ * results, bit for bit, as the unstaged form); should a tile's copies not arrive within
+ * one second, the paths that block had left get NaN gradients instead of a hang. */
 sbr_status sbr_unfold_bwd(sbr_ctx *ctx, const sbr_scene *scene, int64_t npaths, const float *tx,
                           const float *rx, const float *az_el, const int32_t *faces, const int32_t *order,
                           const float *grad_out, float *grad_tx, float *grad_rx, float *grad_az_el);
