@@ -607,7 +607,7 @@ sbr_status sbr_rx_upload(sbr_ctx *ctx, const float *rx, int32_t nrx, sbr_rxset *
         if (!std::isfinite(v)) return fail(ctx, SBR_EINVAL, "sbr_rx_upload: non-finite receiver coordinate");
     BvhOut bvh;
     std::string err;
-    if (!build_bvh(host, host, 4, bvh, err)) return fail(ctx, SBR_EINVAL, err);
+    if (!build_bvh(host, host, 1, bvh, err)) return fail(ctx, SBR_EINVAL, err);
     if (bvh.max_stack4 > kStack4) return fail(ctx, SBR_EINVAL, "sbr_rx_upload: receiver BVH too deep");
     std::vector<float4> pts((size_t)std::max(nrx, 1)), by_id((size_t)std::max(nrx, 1));
     sbr_rxset *rs = new (std::nothrow) sbr_rxset();
