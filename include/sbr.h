@@ -399,9 +399,8 @@ sbr_status sbr_unfold_bwd(sbr_ctx *ctx, const sbr_scene *scene, int64_t npaths, 
 
 /* ---------------------------------------------------------------- allocation-free dedup */
 /* The paper has no counterpart of this entry point; it serves callers that cannot let the
- * library allocate: code being captured into a CUDA graph (cudaMalloc / cudaFree are not
- * allowed during stream capture) and processes whose device memory is fully reserved by
- * another framework's pool.
+ * library allocate device memory while they call it, e.g. processes whose device memory is
+ * fully reserved by another framework's pool.
  *
  * sbr_dedup_noalloc repeats the double-count removal of sbr_launch on the reception
  * records that the last sbr_launch left in `src`, writing the unique paths to `out`

@@ -1,9 +1,8 @@
 // noalloc.cu -- sbr_dedup_noalloc: double-count removal that allocates nothing.
 //
-// Some callers cannot let a library allocate device memory while they call it: code
-// that is being captured into a CUDA graph (cudaMalloc and cudaFree are not allowed
-// during stream capture), and processes whose device memory is already fully reserved
-// by another framework's pool, where an allocation would fail or fragment the pool.
+// Some callers cannot let a library allocate device memory while they call it, e.g.
+// processes whose device memory is already fully reserved by another framework's pool,
+// where an allocation would fail or fragment the pool.
 // For them this entry point keeps its scratch -- the hash table that picks one path per
 // (Tx, Rx, face sequence) -- in a fixed-size array in device global memory that is part
 // of the library image.  The caller passes the input (a container filled by sbr_launch)

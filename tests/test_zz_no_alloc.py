@@ -1,6 +1,6 @@
 """GPU test of sbr_dedup_noalloc, the entry point for callers that cannot let the library
-allocate device memory (code under CUDA stream capture, where cudaMalloc/cudaFree are
-forbidden, and processes whose device memory is reserved by another framework's pool).
+allocate device memory (e.g. processes whose device memory is reserved by another
+framework's pool).
 
 It is called straight through the C ABI and must reproduce the double-count removal that
 sbr_launch performed on the same reception records, on two calls in a row (the fixed
