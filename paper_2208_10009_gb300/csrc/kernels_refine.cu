@@ -350,6 +350,11 @@ __device__ __forceinline__ bool stalled32(float key, float dw, float Rf, float s
     return atan2f(sqrtf(key), dw) > Rf * stall + 1e-6f;
 }
 
+// Why an iteration loop ended before its cap: the accuracy target met, or the error left
+// the stall bound (a redundant path); recorded where the loop exits, so that the path's
+// flags name the test that stopped it, in the precision it was taken in.
+constexpr int kStopNone = 0, kStopReached = 1, kStopStalled = 2;
+
 // Eq. 3 error angle from key and d . W, in the precision of the phase that produced them
 __device__ __forceinline__ double error_angle(double key, double dw, float keyf, float dwf, bool fp64) {
     if (fp64) return key < INFINITY ? atan2(sqrt(key), dw) : INFINITY;
@@ -829,11 +834,19 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
         bool fp64 = Rf < A.fp64_below_f, fail = false;
         float3 cf = make_float3((float)p.dir[0], (float)p.dir[1], (float)p.dir[2]);
         float keyf = INFINITY, dwf = 0.0f;
-        int it = 0, flags = 0;
+        int it = 0, flags = 0, stop = kStopNone;
         if (!fp64) {
             keyf = key32(uf, g.k, cf, dwf);
-            while (it < A.max_iters && !reached32(A, g, uf, cf, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
-                   !(Rf < A.fp64_below_f)) {
+            while (it < A.max_iters) {
+                if (reached32(A, g, uf, cf, keyf, dwf)) {
+                    stop = kStopReached;
+                    break;
+                }
+                if (stalled32(keyf, dwf, Rf, stallf)) {
+                    stop = kStopStalled;
+                    break;
+                }
+                if (Rf < A.fp64_below_f) break;   // on to the FP64 iterations
                 const int ax = A.choice_log ? frame_axis32(cf) : 0;
                 const int bk = iterate32(uf, g.k, A.K, off, Rf, cf, keyf, dwf);
                 if (bk < 0) {
@@ -856,7 +869,16 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
                 key = keyf;
                 dw = dwf;
             }
-            while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
+            stop = kStopNone;   // the FP64 phase judges the state again
+            while (it < A.max_iters) {
+                if (reached(A, g, ud, c, key, dw)) {
+                    stop = kStopReached;
+                    break;
+                }
+                if (stalled(key, dw, R, stall)) {
+                    stop = kStopStalled;
+                    break;
+                }
                 const int ax = A.choice_log ? frame_axis64(c) : 0;
                 const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
                 if (bk < 0) {
@@ -871,8 +893,7 @@ __global__ void __launch_bounds__(256) refine_kernel(RefineArgs A) {
             }
         }
         if (fail) flags |= SBR_PATH_TRACE_FAIL;
-        else if (it < A.max_iters && !(fp64 ? reached(A, g, ud, c, key, dw) : reached32(A, g, uf, cf, keyf, dwf)))
-            flags |= SBR_PATH_STALLED;
+        else if (stop == kStopStalled) flags |= SBR_PATH_STALLED;
         p.iters = it;
         p.flags = flags | (it > 0 ? SBR_PATH_REFINED : 0);
         p.dir[0] = c.x;
@@ -1055,7 +1076,7 @@ __device__ void group_finalize(const RefineArgs &A, const PathGeo &g, dvec3 c, s
 // shuffles, no re-evaluation of the winner) and always runs with batch_unfold_kernel and
 // the FP64 tail kernel (the host sets split_min = 0 for it).
 template <int G>
-__global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(RefineArgs A) {
+__global__ void __launch_bounds__(256, 3) batch_refine_kernel(RefineArgs A) {
     // the unfolded planes of each group's current path (shared by its G lanes)
     __shared__ UnfD s_ud[G == 1 ? 1 : 256 / G];
     __shared__ UnfF s_uf[256 / G];
@@ -1124,11 +1145,19 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
         float Rf = fmaxf(A.theta_launch, p.rough_err);
         bool fp64 = Rf < A.fp64_below_f, fail = false;
         float keyf = INFINITY, dwf = 0.0f;
-        int it = 0, flags = 0;
+        int it = 0, flags = 0, stop = kStopNone;
         if (!fp64) {
             keyf = key32(uf, g.k, cf, dwf);
-            while (it < A.max_iters && !reached32(A, g, uf, cf, keyf, dwf) && !stalled32(keyf, dwf, Rf, stallf) &&
-                   !(Rf < A.fp64_below_f)) {
+            while (it < A.max_iters) {
+                if (reached32(A, g, uf, cf, keyf, dwf)) {
+                    stop = kStopReached;
+                    break;
+                }
+                if (stalled32(keyf, dwf, Rf, stallf)) {
+                    stop = kStopStalled;
+                    break;
+                }
+                if (Rf < A.fp64_below_f) break;   // on to the FP64 iterations
                 const int ax = A.choice_log ? frame_axis32(cf) : 0;
                 const int bk = G == 1 ? iterate32(uf, g.k, A.K, off, Rf, cf, keyf, dwf)
                                       : group_iterate32<G>(uf, g.k, A.K, off, Rf, cf, keyf, dwf, gl, gmask);
@@ -1172,7 +1201,16 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
                 key = keyf;
                 dw = dwf;
             }
-            while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
+            stop = kStopNone;   // the FP64 phase judges the state again
+            while (it < A.max_iters) {
+                if (reached(A, g, ud, c, key, dw)) {
+                    stop = kStopReached;
+                    break;
+                }
+                if (stalled(key, dw, R, stall)) {
+                    stop = kStopStalled;
+                    break;
+                }
                 const int ax = A.choice_log ? frame_axis64(c) : 0;
                 const int bk = group_iterate64<G>(ud, g.k, A.K, off, R, c, key, dw, gl, gmask);
                 if (bk < 0) {
@@ -1187,8 +1225,7 @@ __global__ void __launch_bounds__(256, G == 1 ? 2 : 3) batch_refine_kernel(Refin
             }
         }
         if (fail) flags |= SBR_PATH_TRACE_FAIL;
-        else if (it < A.max_iters && !(fp64 ? reached(A, g, ud, c, key, dw) : reached32(A, g, uf, cf, keyf, dwf)))
-            flags |= SBR_PATH_STALLED;
+        else if (stop == kStopStalled) flags |= SBR_PATH_STALLED;
         if (gl == 0) {
             if (!fp64) c = dv(cf.x, cf.y, cf.z);
             p.iters = it;
@@ -1239,14 +1276,9 @@ __global__ void __launch_bounds__(128) batch_refine64_kernel(RefineArgs A) {
         PathGeo g;
         load_path(A, p, g);
         UnfD ud;
-        UnfF uf;
         const float4 *u = A.unf + kUnfStride * pi;
-        for (int j = 0; j < g.k; ++j) {
-            ud.p[j] = unfold_plane(A.scene, g, j);
-            uf.p[j] = u[j];
-        }
+        for (int j = 0; j < g.k; ++j) ud.p[j] = unfold_plane(A.scene, g, j);
         ud.w = unfold_rx(A.scene, g);
-        uf.w = u[kMaxOrder];
         const float4 cu = u[kMaxOrder + 1];
         const float3 cf = f3(cu);
         const float keyf = cu.w, dwf = (float)p.err;
@@ -1263,7 +1295,16 @@ __global__ void __launch_bounds__(128) batch_refine64_kernel(RefineArgs A) {
             key = keyf;
             dw = dwf;
         }
-        while (it < A.max_iters && !reached(A, g, ud, c, key, dw) && !stalled(key, dw, R, stall)) {
+        int stop = kStopNone;
+        while (it < A.max_iters) {
+            if (reached(A, g, ud, c, key, dw)) {
+                stop = kStopReached;
+                break;
+            }
+            if (stalled(key, dw, R, stall)) {
+                stop = kStopStalled;
+                break;
+            }
             const int ax = A.choice_log ? frame_axis64(c) : 0;
             const int bk = iterate64(ud, g.k, A.K, off, R, c, key, dw);
             if (bk < 0) {
@@ -1277,8 +1318,7 @@ __global__ void __launch_bounds__(128) batch_refine64_kernel(RefineArgs A) {
             ++it;
         }
         if (fail) flags |= SBR_PATH_TRACE_FAIL;
-        else if (it < A.max_iters && !(fp64 ? reached(A, g, ud, c, key, dw) : reached32(A, g, uf, cf, keyf, dwf)))
-            flags |= SBR_PATH_STALLED;
+        else if (stop == kStopStalled) flags |= SBR_PATH_STALLED;
         if (!fp64) c = dv(cf.x, cf.y, cf.z);
         const double err = error_angle(key, dw, keyf, dwf, fp64);
         list_for_finalize(A, g, pi, err, R);

@@ -31,6 +31,16 @@ def gpu_paths_by_key(recs):
     return out
 
 
+def in_key_order(recs, *aligned):
+    """Query output sorted by path key (Tx, Rx, order, face sequence), with arrays aligned to
+    it (e.g. the choice log, indexed like the records) reordered the same way.  The order of
+    sbr_query's output follows the double-count removal's atomics and varies from run to
+    run; a test that samples from it by position samples the same paths only in key order."""
+    o = np.lexsort(tuple(recs["faces"][:, j] for j in range(recs["faces"].shape[1] - 1, -1, -1)) +
+                   (recs["order"], recs["rx"], recs["tx"]))
+    return (recs[o],) + tuple(a[: len(recs)][o] for a in aligned)
+
+
 def oracle_paths_by_key(paths):
     return {(p["tx"], p["rx"], p["order"], tuple(p["faces"])): p for p in paths}
 

@@ -222,7 +222,7 @@ def test_diffraction_full_canyon(gpu_ctx, oracle_mod):
     valid = {k: p for k, p in got.items() if p["valid"]}
     assert len(valid) > 50
     rng = np.random.default_rng(11)
-    keys = list(valid)
+    keys = sorted(valid)   # the query's order varies from run to run
     for i in rng.choice(len(keys), size=min(60, len(keys)), replace=False):
         t, r, w = keys[i]
         ex = oracle_mod.wedge_image(S, tx[t], rx[r], w)

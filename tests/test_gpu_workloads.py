@@ -6,9 +6,10 @@ import numpy as np
 import pytest
 import torch
 
-from paper_2208_10009_gb300 import scenes
+from paper_2208_10009_gb300 import api, scenes
 
-from parity_util import EDGE_MARGIN, TOL_ANGLE_RAD, TOL_DELAY_REL, ang, dir_of, replay_refinement
+from parity_util import (EDGE_MARGIN, PATH_STALLED, PATH_TRACE_FAIL, TOL_ANGLE_RAD, TOL_DELAY_REL, ang, dir_of,
+                         in_key_order, replay_refinement)
 
 
 def _bound(oracle_mod, n, K, r):
@@ -63,8 +64,7 @@ def test_canyon_paths_vs_image_method_and_oracle(gpu_ctx, oracle_mod, canyon):
     gpu_ctx.launch(scene, tx, rxs, paths, n, order, rx_angle_scale=SQ3, sync=True)
     choice = torch.full((paths.path_cap, iters), -1, dtype=torch.int8, device="cuda")
     gpu_ctx.batch_refine(scene, paths, iters, K, choice_log=choice)
-    got = gpu_ctx.query(paths)
-    ch = choice.cpu().numpy()
+    got, ch = in_key_order(gpu_ctx.query(paths), choice.cpu().numpy())
     assert len(got) > 300
     S = oracle_mod.Scene.from_generated(sc)
     valid = got[got["valid"] == 1]
@@ -128,15 +128,25 @@ def test_office_batched(gpu_ctx, oracle_mod):
     gpu_ctx.launch(scene, tx, rxs, paths, n, order, rx_angle_scale=SQ3, sync=True)
     choice = torch.full((paths.path_cap, cap), -1, dtype=torch.int8, device="cuda")
     gpu_ctx.batch_refine(scene, paths, cap, K, target=ACC, choice_log=choice)
-    got = gpu_ctx.query(paths)
-    ch = choice[: len(got)].cpu().numpy()
+    got, ch = in_key_order(gpu_ctx.query(paths), choice.cpu().numpy())
     assert len(got) > 10000
     assert np.all(got["iters"] <= cap)
     its = np.bincount(got["iters"], minlength=cap + 1)
     assert its[1:].sum() > 0 and np.count_nonzero(its) >= 3     # uneven iteration counts
+    tl = np.float32(oracle_mod.theta_launch(n))
+    # every path: a path flagged as stalled has its error above the stall bound of its last
+    # cone (R0 s^iters (1 / (1 - s) + 2 s) + 1e-6, the test that stopped it), and a path that
+    # stopped before the cap without stalling met the target (AOD error within 0.01 deg)
+    s = api.subray_pattern(K)[2]
+    R = np.maximum(tl, got["rough_err"]).astype(np.float64) * s ** got["iters"].astype(np.float64)
+    bound = R * (1.0 / (1.0 - s) + 2.0 * s) + 1e-6
+    ok = (got["flags"] & PATH_TRACE_FAIL) == 0
+    st = ok & ((got["flags"] & PATH_STALLED) != 0)
+    assert np.all(got["err"][st] > bound[st] * (1 - 1e-5)), np.nonzero(got["err"][st] <= bound[st] * (1 - 1e-5))
+    early = ok & ~st & (got["iters"] < cap) & (got["iters"] > 0)
+    assert np.all(got["err"][early] <= ACC * (1 + 1e-4))
     S = oracle_mod.Scene.from_generated(sc)
     rng = np.random.default_rng(1)
-    tl = np.float32(oracle_mod.theta_launch(n))
     marginal = ties = early = 0
     for i in rng.choice(len(got), size=400, replace=False):
         r = got[i]
@@ -265,7 +275,7 @@ def test_large_city_sampled(gpu_ctx, oracle_mod):
     # refined far below 0.01 deg (n = 2200 rough rays already meet it) so that the
     # validity test sees bounce points within millimetres of the exact ones
     gpu_ctx.batch_refine(scene, paths, 16, 9)
-    got = gpu_ctx.query(paths)
+    (got,) = in_key_order(gpu_ctx.query(paths))
     assert len(got) > 1000
     rng = np.random.default_rng(5)
     valid = got[got["valid"] == 1]
