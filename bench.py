@@ -504,9 +504,9 @@ def run_gpu(args):
 
 
 def _launches_per_step(opts, world):
-    """Library kernels per step: raygen, trace (+2 diffraction), 4 dedup, 4 batched
-    refinement; shards add the record-count reset kernel."""
-    return 10 + (2 if opts["diffraction"] else 0) + (1 if world > 1 else 0)
+    """Library kernels per step: raygen, trace (+3 diffraction: candidates, receivers,
+    occlusion), 4 dedup, 4 batched refinement; shards add the record-count reset kernel."""
+    return 10 + (3 if opts["diffraction"] else 0) + (1 if world > 1 else 0)
 
 
 def _refine_forms(ctx, scene, paths, relaunch, stream, iters, K, target, shape, ntx, nrx, trials=3):

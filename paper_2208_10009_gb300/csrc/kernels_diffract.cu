@@ -180,13 +180,22 @@ __global__ void __launch_bounds__(128) diffract_candidates(DiffractArgs A) {
 // Pass 2, 32 candidates per warp: each lane checks that its candidate's edge point is
 // visible from Tx; then for every visible candidate the whole warp tests the receivers
 // (lane-strided): exterior, unfolded error angle within the cone, unblocked X -> Rx.
+// Receptions waiting for their occlusion query (diffract_occlusion) are parked at the top of
+// the record array, slot rec_cap - 1 - q for the q-th, while the final records grow from
+// the trace's count n0 at the bottom; parking q < (rec_cap - n0) / 2 of them leaves room for
+// all of them as final records, so the two ends never meet.  Past that bound the launch
+// reports record overflow (the record count is raised above the capacity).
+__device__ __forceinline__ long long park_limit(const DiffractArgs &A, long long n0) { return (A.rec_cap - n0) / 2; }
+
 __global__ void __launch_bounds__(256) diffract_receive(DiffractArgs A) {
     const SceneDev &S = A.scene;
     long long ncand = A.counters[kDiffCand];
     if (ncand > A.cand_cap) ncand = A.cand_cap;
+    const long long n0 = A.counters[kRecords];   // the trace's records; nothing appends here
+    const long long limit = park_limit(A, n0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) A.counters[kDiffBase] = n0;
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    unsigned emitted = 0;
     for (long long base = (long long)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < ncand;
          base += warps * 32) {
         const long long c = base + lane;
@@ -238,24 +247,70 @@ __global__ void __launch_bounds__(256) diffract_receive(DiffractArgs A) {
                 if (!(dw > 0.0f) || cc > dw * dw * t2) continue;
                 const float err = atan2f(sqrtf(cc), dw);
                 if (!(err <= A.cone)) continue;
-                if (any_hit4(S, make_ray(X, R - X), 1e-6f, 1.0f - 1e-6f, w.f1, w.f2)) continue;
-                unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kRecords), 1ULL);
-                ++emitted;
-                if ((long long)slot >= A.rec_cap) continue;
+                // the segment X -> Rx is tested by diffract_occlusion, a query per thread in
+                // full warps (here it would run in one lane while the warp waits); the
+                // reception is parked with X in its unused face slots 1-3
+                const long long pq = (long long)atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kDiffPending), 1ULL);
+                if (pq >= limit) {
+                    atomicMax(reinterpret_cast<unsigned long long *>(A.counters + kRecords),
+                              (unsigned long long)A.rec_cap + 1ULL);
+                    continue;
+                }
                 RecDev rec;
                 rec.tx = txi;
                 rec.rx = rx;
                 rec.ray = ray;
                 rec.order = 1;
                 rec.faces[0] = -1 - id;
+                rec.faces[1] = __float_as_int(X.x);
+                rec.faces[2] = __float_as_int(X.y);
+                rec.faces[3] = __float_as_int(X.z);
 #pragma unroll
-                for (int j = 1; j < kMaxOrder; ++j) rec.faces[j] = -1;
+                for (int j = 4; j < kMaxOrder; ++j) rec.faces[j] = -1;
                 rec.err = err;
                 rec.dray = sqrtf(dot(W, W)) * cosf(err);
                 rec.slot = -1;
                 rec.pad = 0;
-                A.recs[slot] = rec;
+                A.recs[A.rec_cap - 1 - pq] = rec;
             }
+        }
+    }
+}
+
+// The occlusion queries of the parked diffraction receptions: a reception whose segment from
+// the edge point X to Rx is unblocked (the wedge's two faces excluded) becomes a record,
+// appended with one atomic per warp; blocked ones are dropped.
+__global__ void __launch_bounds__(128) diffract_occlusion(DiffractArgs A) {
+    const SceneDev &S = A.scene;
+    long long P = A.counters[kDiffPending];
+    const long long limit = park_limit(A, A.counters[kDiffBase]);
+    if (P > limit) P = limit;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    unsigned emitted = 0;
+    for (long long base = (long long)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < P;
+         base += warps * 32) {
+        const long long q = base + lane;
+        RecDev rec;
+        bool keep = false;
+        if (q < P) {
+            rec = A.recs[A.rec_cap - 1 - q];
+            const float3 X = make_float3(__int_as_float(rec.faces[1]), __int_as_float(rec.faces[2]),
+                                         __int_as_float(rec.faces[3]));
+            const float3 R = f3(__ldg(A.rx.by_id + rec.rx));
+            const WedgeF w = load_wedge(S, -1 - rec.faces[0]);
+            keep = !any_hit4(S, make_ray(X, R - X), 1e-6f, 1.0f - 1e-6f, w.f1, w.f2);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, keep);
+        if (!b) continue;
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(reinterpret_cast<unsigned long long *>(A.counters + kRecords), (unsigned long long)__popc(b));
+        at = __shfl_sync(0xffffffffu, at, 0) + __popc(b & lt);
+        if (keep) {
+            rec.faces[1] = rec.faces[2] = rec.faces[3] = -1;
+            if ((long long)at < A.rec_cap) A.recs[at] = rec;
+            ++emitted;
         }
     }
     emitted = __reduce_add_sync(0xffffffffu, emitted);
@@ -266,6 +321,7 @@ cudaError_t launch_diffract(const DiffractArgs &a, int num_sms, cudaStream_t s) 
     if (a.scene.nw == 0 || a.rx.nrx == 0) return cudaSuccess;
     diffract_candidates<<<num_sms * 8, 128, 0, s>>>(a);
     diffract_receive<<<num_sms * 4, 256, 0, s>>>(a);
+    diffract_occlusion<<<num_sms * 8, 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 

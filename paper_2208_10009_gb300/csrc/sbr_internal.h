@@ -30,7 +30,9 @@ constexpr int kStack4 = 96;        // 4-wide traversal stack (the builder checks
 enum Counter {
     kRays = 0, kSegments, kNodeVisits, kTriTests, kRxTests, kRecords, kPaths, kCollisions,
     kRayHead, kBatchHead, kBatchDone, kErrorFlags, kWedgeTests, kDiffRecords, kDiffCand, kNonFinite,
-    kNumCounters = 16
+    kDiffPending,   // diffraction receptions parked at the top of the record array for diffract_occlusion
+    kDiffBase,      // the record count before them (the trace's records)
+    kNumCounters = 18
 };
 
 // BVH node: both children's boxes in one 64-byte node (4 x float4).
