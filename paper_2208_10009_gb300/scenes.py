@@ -276,3 +276,49 @@ def large_city(seed=SEED_BASE + 5, blocks=60, pitch=55.0, terrain_cells=700, ntx
 def jitter(rng, pts, amount):
     """Uniform +-amount jitter of every coordinate (float32-exact)."""
     return f32_exact(pts + rng.uniform(-amount, amount, np.shape(pts)))
+
+
+# --------------------------------------------------------------------------- random clutter
+def _rotation(rng) -> np.ndarray:
+    """A uniformly random rotation matrix (from a random unit quaternion)."""
+    q = rng.normal(size=4)
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def random_clutter(seed=SEED_BASE + 9, nbox=20, room=(20.0, 16.0, 6.0), g_room=2, nrx=4):
+    """Seeded closed room (each wall g_room x g_room quads) holding `nbox` boxes of random
+    size (0.6-2.5 m per side) in arbitrary orientations, each box side its own face, so that
+    no face lies on a coordinate plane; boxes may interpenetrate.  Tx and `nrx` Rx at random
+    positions at least 0.3 m outside every box.  Returns (scene, tx (1, 3), rx (nrx, 3))."""
+    rng = np.random.default_rng(seed)
+    L, W, H = room
+    b = _Builder()
+    box_faces(b, (0.0, 0.0, 0.0), (L, W, H), g_room)
+    frames = []
+    for _ in range(nbox):
+        half = rng.uniform(0.3, 1.25, 3)
+        Rm = _rotation(rng)
+        r = float(np.linalg.norm(half))
+        c = np.array([rng.uniform(r, L - r), rng.uniform(r, W - r), rng.uniform(r, H - r)])
+        corner = lambda sx, sy, sz: c + Rm @ (half * np.array([sx, sy, sz]))
+        # the six sides as parallelograms p0 + u (p1 - p0) + v (p3 - p0)
+        for s in (-1.0, 1.0):
+            b.quad(corner(s, -1, -1), corner(s, 1, -1), corner(s, -1, 1))
+            b.quad(corner(-1, s, -1), corner(1, s, -1), corner(-1, s, 1))
+            b.quad(corner(-1, -1, s), corner(1, -1, s), corner(-1, 1, s))
+        frames.append((c, Rm, half))
+    sc = b.finish(name="random_clutter", seed=seed, nbox=nbox)
+
+    def free(p):
+        return all(np.any(np.abs(Rm.T @ (p - c)) > half + 0.3) for c, Rm, half in frames)
+
+    pts = []
+    while len(pts) < 1 + nrx:
+        p = rng.uniform([0.5, 0.5, 0.5], [L - 0.5, W - 0.5, H - 0.5])
+        if free(p):
+            pts.append(p)
+    pts = np.array(pts)
+    return sc, f32_exact(pts[:1]), f32_exact(pts[1:])
