@@ -32,7 +32,8 @@ def _tetra():
                                   lambda: _box((0, 0, 0), (2, 3, 4), g=3, bottom=False),
                                   _tetra,
                                   lambda: scenes.urban_canyon(blocks=3)[0],
-                                  lambda: scenes.office(nbox=40, ntx=1, nrx=3, g_shell=4, g_box=3)[0]])
+                                  lambda: scenes.office(nbox=40, ntx=1, nrx=3, g_shell=4, g_box=3)[0],
+                                  lambda: scenes.random_clutter(scenes.SEED_BASE + 10)[0]])
 def test_wedges_match_oracle(gpu_ctx, oracle_mod, make):
     sc = make()
     scene = gpu_ctx.scene_from(sc)
@@ -233,5 +234,54 @@ def test_diffraction_full_canyon(gpu_ctx, oracle_mod):
         exact = set(oracle_mod.wedge_enumerate(S, tx[0], rx[r]))
         found = {w for (t, rr, w) in valid if rr == r}
         assert found == exact, (r, sorted(exact - found), sorted(found - exact))
+    for h in (paths, rxs, scene):
+        h.close()
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_diffraction_random_clutter(gpu_ctx, oracle_mod, seed):
+    """Wedges at arbitrary orientations (a room holding rotated, interpenetrating boxes):
+    the rough diffraction paths equal the oracle's brute-force search (keys, winning ray and
+    error angle, apart from decisions within rounding of a threshold), and after 20
+    iterations the validity flags equal the oracle's, every valid path matches its exact
+    diffraction point (AOD, AOA, delay, power) and the valid set is the exact valid set."""
+    sc, tx, rx = scenes.random_clutter(scenes.SEED_BASE + 9 + seed)
+    n = 48
+    S = oracle_mod.Scene.from_generated(sc)
+    scene = gpu_ctx.scene_from(sc)
+    rxs = gpu_ctx.rx_upload(rx)
+    paths = gpu_ctx.paths_create(1 << 18, 1 << 14)
+    cone = SQ3 * oracle_mod.theta_launch(n)
+    dr = oracle_mod.diffract(S, tx[0], oracle_mod.lattice(n), rx, cone)
+    ora = {(p["tx"], p["rx"], p["wedge"]): p for p in oracle_mod.dedup_wedge(dr, 0)}
+    gpu_ctx.launch(scene, tx, rxs, paths, n, 0, rx_angle_scale=SQ3, sync=True, diffraction=True)
+    got = _diff_paths(gpu_ctx.query(paths))
+    assert len(ora) > 10
+    only_gpu, only_ora = set(got) - set(ora), set(ora) - set(got)
+    assert len(only_gpu) + len(only_ora) <= max(2, len(ora) // 50), (sorted(only_gpu), sorted(only_ora))
+    both = set(got) & set(ora)
+    same = [k for k in both if int(got[k]["ray"]) == ora[k]["ray"]]
+    assert len(same) >= 0.97 * len(both)
+    for k in same:
+        assert abs(got[k]["rough_err"] - ora[k]["err"]) < 1e-6 * cone + 2e-7, k
+    gpu_ctx.batch_refine(scene, paths, 20, 9)
+    got = _diff_paths(gpu_ctx.query(paths))
+    tl = oracle_mod.theta_launch(n)
+    checked = 0
+    for (t, r, w), p in got.items():
+        R0 = max(tl, float(p["rough_err"]))
+        ev = oracle_mod.wedge_eval(S, tx[t], rx[r], w, p["dir"], err_bound=oracle_mod.refined_err_bound(R0, 9, int(p["iters"])))
+        assert bool(p["valid"]) == ev["valid"], ((t, r, w), p["valid"], ev)
+        if p["valid"]:
+            ex = oracle_mod.wedge_image(S, tx[t], rx[r], w)
+            assert ex["valid"]
+            assert ang(p["dir"], ex["aod_dir"]) < TOL_ANGLE_RAD
+            assert ang(dir_of(*p["aoa"]), dir_of(*ex["aoa"])) < TOL_ANGLE_RAD
+            assert abs(p["delay"] / ex["delay"] - 1) < TOL_DELAY_REL
+            assert abs(p["power_dbm"] - ex["power"]) < 1e-3
+            checked += 1
+    exact = {(0, r, w) for r in range(len(rx)) for w in oracle_mod.wedge_enumerate(S, tx[0], rx[r])}
+    valid = {k for k, p in got.items() if p["valid"]}
+    assert valid == exact and checked > 5
     for h in (paths, rxs, scene):
         h.close()
