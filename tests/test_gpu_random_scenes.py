@@ -1,14 +1,15 @@
 """a2-a8 parity on seeded random scenes whose faces lie on no coordinate plane: a room with
 twenty arbitrarily rotated, interpenetrating boxes.  Every ray's face sequence and every
-reception record against the oracle's brute-force trace, and every refined path's
-validity and outputs against the oracle and the image method."""
+reception record against the oracle's brute-force trace, every refinement decision against
+the oracle's replay, and every refined path's validity and outputs against the oracle and
+the image method."""
 import numpy as np
 import pytest
 import torch
 
 from paper_2208_10009_gb300 import scenes
 
-from parity_util import EDGE_MARGIN, ang, dir_of
+from parity_util import EDGE_MARGIN, ang, dir_of, in_key_order, replay_refinement
 
 pytestmark = pytest.mark.gpu
 SQ3 = float(np.sqrt(3.0))
@@ -62,12 +63,19 @@ def test_random_clutter_every_ray_and_path(gpu_ctx, oracle_mod, seed):
     # refined paths: validity on the GPU's own direction equals the oracle's; valid paths
     # with an exact image-method counterpart agree with it (AOD within 0.01 deg, delay within
     # 1e-6; AOA within 0.01 deg where the early stop ended the refinement)
-    gpu_ctx.batch_refine(scene, paths, cap, K, target=ACC)
-    got = gpu_ctx.query(paths)
+    choice = torch.full((paths.path_cap, cap), -1, dtype=torch.int8, device="cuda")
+    gpu_ctx.batch_refine(scene, paths, cap, K, target=ACC, choice_log=choice)
+    got, ch = in_key_order(gpu_ctx.query(paths), choice.cpu().numpy())
     assert len(got) > 20
     n_valid = n_im = 0
-    for r in got:
+    tl = np.float32(oracle_mod.theta_launch(n))
+    for i, r in enumerate(got):
         faces = tuple(int(f) for f in r["faces"][: r["order"]])
+        # every decision of the refinement (argmin, frame axis, stop) against the oracle's
+        # FP64 replay of the same decisions
+        c0 = oracle_mod.lattice_ids(n, [int(r["ray"])])[0]
+        replay_refinement(oracle_mod, S, tx[0], rx[r["rx"]], faces, c0, max(float(tl), float(r["rough_err"])), K, r,
+                          ch[i], cap, ACC)
         R0 = max(oracle_mod.theta_launch(n), float(r["rough_err"]))
         bound = oracle_mod.refined_err_bound(R0, K, int(r["iters"])) if r["iters"] > 0 else 0.0
         ev = oracle_mod.path_eval(S, tx[0], rx[r["rx"]], faces, r["dir"], err_bound=bound)
