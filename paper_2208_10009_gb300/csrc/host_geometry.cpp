@@ -77,36 +77,57 @@ struct Builder {
         for (int a = 0; a < 3; ++a) {
             float ext = cb.hi[a] - cb.lo[a];
             if (!(ext > 0.0f)) continue;
-            Box bins[B];
-            int cnt[B] = {0};
+            // only the occupied bins are set up and swept: the split cost is the same for
+            // every bin boundary between two occupied bins, and the first of them (just past
+            // the lower occupied bin) is the one the strict comparison keeps, so the choice
+            // equals a sweep over all B boundaries at a cost that follows the node's size
+            struct BinBox {
+                float lo[3], hi[3];
+            } bins[B];   // set when a bin is first occupied
+            int cnt[B];
+            unsigned occ = 0;
             float scale = B / ext;
             for (int i = first; i < first + count; ++i) {
                 int p = idx[i];
                 int k = std::min(B - 1, (int)((cen[3 * p + a] - cb.lo[a]) * scale));
-                bins[k].grow(&lo[3 * p], &hi[3 * p]);
+                BinBox &bb = bins[k];
+                if (!(occ >> k & 1u)) {
+                    occ |= 1u << k;
+                    for (int e = 0; e < 3; ++e) {
+                        bb.lo[e] = lo[3 * p + e];
+                        bb.hi[e] = hi[3 * p + e];
+                    }
+                    cnt[k] = 1;
+                    continue;
+                }
+                for (int e = 0; e < 3; ++e) {
+                    bb.lo[e] = std::min(bb.lo[e], lo[3 * p + e]);
+                    bb.hi[e] = std::max(bb.hi[e], hi[3 * p + e]);
+                }
                 ++cnt[k];
             }
+            int ob[B], no = 0;
+            for (unsigned m = occ; m; m &= m - 1) ob[no++] = __builtin_ctz(m);
             float right_area[B];
             int right_cnt[B];
             Box acc;
             int c = 0;
-            for (int k = B - 1; k > 0; --k) {
-                acc.grow(bins[k]);
-                c += cnt[k];
-                right_area[k] = acc.area();
-                right_cnt[k] = c;
+            for (int j = no - 1; j >= 1; --j) {   // right side of the boundary below ob[j]
+                acc.grow(bins[ob[j]].lo, bins[ob[j]].hi);
+                c += cnt[ob[j]];
+                right_area[j] = acc.area();
+                right_cnt[j] = c;
             }
             Box lacc;
             int lc = 0;
-            for (int k = 1; k < B; ++k) {
-                lacc.grow(bins[k - 1]);
-                lc += cnt[k - 1];
-                if (lc == 0 || right_cnt[k] == 0) continue;
-                float cost = lacc.area() * lc + right_area[k] * right_cnt[k];
+            for (int j = 1; j < no; ++j) {
+                lacc.grow(bins[ob[j - 1]].lo, bins[ob[j - 1]].hi);
+                lc += cnt[ob[j - 1]];
+                float cost = lacc.area() * lc + right_area[j] * right_cnt[j];
                 if (cost < best_cost) {
                     best_cost = cost;
                     best_axis = a;
-                    best_split = k;
+                    best_split = ob[j - 1] + 1;
                 }
             }
         }
