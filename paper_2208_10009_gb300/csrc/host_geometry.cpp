@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <system_error>
+#include <thread>
 
 #include "sbr_internal.h"
 
@@ -37,20 +39,47 @@ struct TmpNode {
     int first = 0, count = 0;
 };
 
+// Right subtrees of at least this many primitives, within this many levels of the root,
+// are built on threads of their own.
+constexpr int kParallelMin = 512, kParallelDepth = 5;
+
 struct Builder {
     const std::vector<float> &lo, &hi;
-    std::vector<float> cen;
-    std::vector<int> idx;
+    const std::vector<float> &cen;   // box centres, shared by the builders of one tree
+    std::vector<int> &idx;           // primitive order, each builder permuting its own range
     std::vector<TmpNode> nodes;
     int leaf_max;
     int depth = 0, max_leaf = 0;
 
-    Builder(const std::vector<float> &l, const std::vector<float> &h, int lm) : lo(l), hi(h), leaf_max(lm) {
-        size_t n = l.size() / 3;
-        cen.resize(3 * n);
-        for (size_t i = 0; i < 3 * n; ++i) cen[i] = 0.5f * (l[i] + h[i]);
-        idx.resize(n);
-        std::iota(idx.begin(), idx.end(), 0);
+    Builder(const std::vector<float> &l, const std::vector<float> &h, const std::vector<float> &c,
+            std::vector<int> &ix, int lm)
+        : lo(l), hi(h), cen(c), idx(ix), leaf_max(lm) {}
+
+    // The right subtree [mid, first + count) on a thread of its own: it partitions only its
+    // own range of idx, and its nodes are appended after the left subtree's, in the order
+    // the serial recursion gives them, so the tree and its numbering do not depend on the
+    // threads.  Returns the subtree's root, or -1 if no thread could be started.
+    int make_split(int first, int count, int mid, int d, int &l) {
+        Builder rb(lo, hi, cen, idx, leaf_max);
+        std::thread th;
+        try {
+            th = std::thread([&rb, mid, first, count, d] { rb.make(mid, first + count - mid, d + 1); });
+        } catch (const std::system_error &) {
+            return -1;
+        }
+        l = make(first, mid - first, d + 1);
+        th.join();
+        const int off = (int)nodes.size();
+        for (TmpNode t : rb.nodes) {
+            if (t.left >= 0) {
+                t.left += off;
+                t.right += off;
+            }
+            nodes.push_back(t);
+        }
+        depth = std::max(depth, rb.depth);
+        max_leaf = std::max(max_leaf, rb.max_leaf);
+        return off;
     }
 
     int make(int first, int count, int d) {
@@ -151,8 +180,12 @@ struct Builder {
             mid = (int)(it - idx.begin());
             if (mid == first || mid == first + count) mid = first + count / 2;
         }
-        int l = make(first, mid - first, d + 1);
-        int r = make(mid, first + count - mid, d + 1);
+        int l = -1, r = -1;
+        if (count >= kParallelMin && d <= kParallelDepth) r = make_split(first, count, mid, d, l);
+        if (r < 0) {
+            l = make(first, mid - first, d + 1);
+            r = make(mid, first + count - mid, d + 1);
+        }
         nodes[id].left = l;
         nodes[id].right = r;
         return id;
@@ -180,7 +213,11 @@ bool build_bvh(const std::vector<float> &lo, const std::vector<float> &hi, int l
         err = "BVH: more than 2^24 primitives";
         return false;
     }
-    Builder b(lo, hi, leaf_max);
+    std::vector<float> cen(3 * n);
+    for (size_t i = 0; i < 3 * n; ++i) cen[i] = 0.5f * (lo[i] + hi[i]);
+    std::vector<int> prims(n);
+    std::iota(prims.begin(), prims.end(), 0);
+    Builder b(lo, hi, cen, prims, leaf_max);
     if (n > 0) b.make(0, (int)n, 1);
     // Flatten: every inner TmpNode becomes one 64-byte node holding its children.
     std::vector<int> flat_id(b.nodes.size(), -1);
