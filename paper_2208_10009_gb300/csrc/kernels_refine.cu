@@ -754,6 +754,9 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
     }
     // Rx must be received on the last leg and the refinement must have converged
     bool valid = rx_ahead(g, last, dl) && p.err <= err_bound;
+    // the outputs need only the first pass: computed now, so that its results are not
+    // held in registers through the occlusion queries
+    path_outputs(A, g, c, last, tsum, gain_db, p);
     // Second pass: the walk again, each bounce point tested on its face and each leg for
     // occlusion as it is reached.  The lanes that arrive here together run the queries in
     // lockstep: loop bounds made uniform over them, a lane that has failed a test idles
@@ -781,7 +784,6 @@ __device__ void finalize_path(const RefineArgs &A, const PathGeo &g, dvec3 c, sb
         if (any_hit4(S, r, 1e-6f, 1.0f - 1e-6f, fa, fb)) valid = false;
     }
     p.valid = valid ? 1 : 0;
-    path_outputs(A, g, c, last, tsum, gain_db, p);
 }
 
 __device__ __forceinline__ void store_result(sbr_path_record *dst, const sbr_path_record &p) {
