@@ -682,7 +682,7 @@ sbr_status sbr_paths_create(sbr_ctx *ctx, int64_t record_cap, int64_t path_cap, 
     cv.add(&p->order_idx, (size_t)path_cap);
     cv.add(&p->order_cnt, (size_t)64);
     cv.add(&p->fp64_idx, (size_t)path_cap);
-    cv.add(&table, (size_t)slots * 2 + (size_t)(slots + 1) / 2);   // keys, values, winner ids
+    cv.add(&table, (size_t)slots * 2 + (size_t)(slots + 1) / 2);   // (key, value) slots, winner ids
     cv.add(&p->counters, (size_t)kNumCounters);
     p->mem = dev_alloc(ctx, cv.total);
     if (!p->mem) {

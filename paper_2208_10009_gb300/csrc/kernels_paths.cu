@@ -19,31 +19,32 @@ __device__ __forceinline__ unsigned long long used_slots(const DedupArgs &a) {
     return dedup_slots(num_records(a), a.slots);
 }
 
-// keys and values to all-ones (empty / +inf), winners to -1, over the used slots
+// A slot is 16 bytes, its key then its value (one 32-byte sector holds two slots, so an
+// insert's compare-and-swap and minimum touch one sector); the winners follow the slots.
+// Keys and values to all-ones (empty / +inf), winners to -1, over the used slots.
 __global__ void dedup_clear(DedupArgs a) {
     const unsigned long long m = used_slots(a);
-    unsigned long long *keys = a.table, *vals = a.table + a.slots;
+    ulonglong2 *slot = reinterpret_cast<ulonglong2 *>(a.table);
     int *winner = reinterpret_cast<int *>(a.table + 2 * a.slots);
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < m;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        keys[i] = ~0ULL;
-        vals[i] = ~0ULL;
+        slot[i] = make_ulonglong2(~0ULL, ~0ULL);
         winner[i] = -1;
     }
 }
 
 __global__ void dedup_insert(DedupArgs a) {
     const long long n = num_records(a);
-    unsigned long long *keys = a.table, *vals = a.table + a.slots;
+    unsigned long long *tab = a.table;   // key of slot s at 2 s, its value at 2 s + 1
     const unsigned long long used = used_slots(a), mask = used - 1;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         RecDev r = a.recs[i];
         unsigned long long h = rec_hash(r), v = rec_value(r);
         unsigned long long s = h & mask;
         for (unsigned long long probe = 0; probe < used; ++probe) {
-            unsigned long long prev = atomicCAS(keys + s, ~0ULL, h);
+            unsigned long long prev = atomicCAS(tab + 2 * s, ~0ULL, h);
             if (prev == ~0ULL || prev == h) {
-                atomicMin(vals + s, v);
+                atomicMin(tab + 2 * s + 1, v);
                 a.recs[i].slot = (int)s;
                 break;
             }
@@ -54,12 +55,12 @@ __global__ void dedup_insert(DedupArgs a) {
 
 __global__ void dedup_select(DedupArgs a) {
     const long long n = num_records(a);
-    const unsigned long long *vals = a.table + a.slots;
+    const unsigned long long *tab = a.table;
     int *winner = reinterpret_cast<int *>(a.table + 2 * a.slots);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         RecDev r = a.recs[i];
         if (r.slot < 0) continue;
-        if (vals[r.slot] != rec_value(r)) continue;
+        if (tab[2 * (long long)r.slot + 1] != rec_value(r)) continue;
         winner[r.slot] = (int)i;
         if (a.shard_world > 1 && (r.tx * a.nrx + r.rx) % a.shard_world != a.shard_rank) continue;
         unsigned long long p = atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kPaths), 1ULL);
@@ -98,6 +99,7 @@ __global__ void dedup_verify(DedupArgs a) {
             continue;
         }
         int w = winner[r.slot];
+        if (w == (int)i) continue;   // the winner itself
         if (w < 0 || !same_key(r, a.recs[w])) ++bad;
     }
     if (bad) atomicAdd(reinterpret_cast<unsigned long long *>(a.counters + kCollisions), (unsigned long long)bad);
