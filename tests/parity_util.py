@@ -2,7 +2,7 @@
 import numpy as np
 
 DEG = np.pi / 180.0
-# tolerances (the benchmark spec): delays 1e-6 relative, angles 1e-4 degree
+# parity tolerances of the GPU path against the oracle: delays 1e-6 relative, angles 1e-4 degree
 TOL_DELAY_REL = 1e-6
 TOL_ANGLE_RAD = 1e-4 * DEG
 # grazing / edge exclusion margin for per-ray face-sequence parity (rad)
