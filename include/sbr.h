@@ -199,6 +199,11 @@ typedef struct {
                                    ids stay the lattice's own (position-independent records) */
 #define SBR_LAUNCH_RECORDS_ONLY 16 /* stop after the reception judgment: the container keeps the
                                       reception records (sbr_records_read) and no paths */
+#define SBR_LAUNCH_ID_ORDER 32 /* trace the rays in lattice id order.  By default a launch of a
+                                  whole equiangular lattice takes them in compact tiles of
+                                  each face's triangular grid (neighbouring directions together
+                                  in a warp); the results are the same either way (§III.A:
+                                  rays are independent) */
 
 typedef struct {
     int64_t rays;            /* rays traced (ntx * N) */

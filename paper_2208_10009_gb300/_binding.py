@@ -65,6 +65,7 @@ LAUNCH_TIMING = 2
 LAUNCH_DIFFRACTION = 4
 LAUNCH_RAY_RANGE = 8
 LAUNCH_RECORDS_ONLY = 16
+LAUNCH_ID_ORDER = 32
 PATH_REFINED, PATH_FP64, PATH_TRACE_FAIL, PATH_DIFFRACTED, PATH_STALLED = 1, 2, 4, 8, 16
 
 PATH_DTYPE = np.dtype([("tx", "<i4"), ("rx", "<i4"), ("ray", "<i4"), ("order", "<i4"), ("faces", "<i4", (MAX_ORDER,)),

@@ -201,12 +201,13 @@ class Context:
                rx_angle_scale: float = 1.0, sync: bool = False, dump_stride: int = 0,
                dump: torch.Tensor | None = None, grid_blocks: int = 0, block_threads: int = 0,
                timing: bool = False, refill_min: int = 0, launcher: int = 0, diffraction: bool = False,
-               ray_range: tuple[int, int] | None = None, records_only: bool = False):
+               ray_range: tuple[int, int] | None = None, records_only: bool = False, id_order: bool = False):
         """a1-a5: ray generation, trace with reception, double-count removal.  `tx` is an
         (ntx, 3) array on the host (numpy) or the device (torch).  `diffraction` adds the
         order-1 diffraction search.  `ray_range` = (begin, end) traces only those ray ids of
         every Tx; `records_only` stops before double-count removal (read the records with
-        `records`)."""
+        `records`).  `id_order` makes the trace take the rays in lattice id order instead of
+        the default compact tiles of directions (the same results)."""
         if isinstance(tx, torch.Tensor):
             txp, ntx = tx.data_ptr(), tx.numel() // 3
             keep = tx
@@ -215,7 +216,7 @@ class Context:
             txp, ntx = keep.ctypes.data, len(keep)
         flags = ((B.LAUNCH_SYNC if sync else 0) | (B.LAUNCH_TIMING if timing else 0) |
                  (B.LAUNCH_DIFFRACTION if diffraction else 0) | (B.LAUNCH_RAY_RANGE if ray_range else 0) |
-                 (B.LAUNCH_RECORDS_ONLY if records_only else 0))
+                 (B.LAUNCH_RECORDS_ONLY if records_only else 0) | (B.LAUNCH_ID_ORDER if id_order else 0))
         rb, re_ = (int(ray_range[0]), int(ray_range[1])) if ray_range else (0, 0)
         prm = B.LaunchParams(n_div, max_order, rx_angle_scale, flags, dump_stride,
                              _ptr(dump), 0 if dump is None else dump.numel(), grid_blocks, block_threads,

@@ -801,6 +801,8 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
     a.dump_faces = prm->dump_faces;
     a.dump_per_tx = prm->dump_stride > 0 ? (N + prm->dump_stride - 1) / prm->dump_stride : 0;
     a.refill_min = prm->refill_min > 0 ? std::min(prm->refill_min, 32) : 24;
+    a.tiled_n = (prm->launcher == 0 && ray_begin == 0 && ray_count == N && !(prm->flags & SBR_LAUNCH_ID_ORDER))
+                    ? prm->n_div : 0;
     int block = prm->block_threads > 0 ? prm->block_threads : 128;
     if (block % 32 != 0 || block > 128)
         return fail(ctx, SBR_EINVAL, "sbr_launch: block_threads must be a multiple of 32, at most 128");

@@ -265,6 +265,8 @@ struct TraceArgs {
     int *dump_faces;
     int64_t dump_per_tx;
     int refill_min;           // a warp takes new rays once at least this many lanes are idle
+    int tiled_n;              // > 0: the launch traces the whole equiangular lattice of this
+                              // division level, in the order of tiled_ray; 0: lattice id order
 };
 cudaError_t launch_trace(const TraceArgs &a, int grid, int block, cudaStream_t s);
 
