@@ -66,8 +66,8 @@ ACC_DEG = 0.01
 FLOP_NODE, FLOP_TRI, FLOP_RX = 48, 40, 20
 L2_FLUSH_BYTES = 256 << 20
 
-TRACE_SOURCES = ["paper_2208_10009_gb300/csrc/kernels_trace.cu", "paper_2208_10009_gb300/csrc/sbr_device.cuh",
-                 "paper_2208_10009_gb300/csrc/sbr_internal.h"]
+TRACE_SOURCES = ["paper_2208_10009_gb300/csrc/kernels_trace.cu", "paper_2208_10009_gb300/csrc/lattice_order.cuh",
+                 "paper_2208_10009_gb300/csrc/sbr_device.cuh", "paper_2208_10009_gb300/csrc/sbr_internal.h"]
 TRAFFIC_FILES = {"canyon": os.path.join(ROOT, "profiles", "trace_kernel_traffic.json"),
                  "city": os.path.join(ROOT, "profiles", "trace_kernel_traffic_large_city.json")}
 UNFOLD_SOURCES = ["paper_2208_10009_gb300/csrc/kernels_unfold.cu", "paper_2208_10009_gb300/csrc/sbr_device.cuh",

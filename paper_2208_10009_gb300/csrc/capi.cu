@@ -829,6 +829,7 @@ sbr_status sbr_launch(sbr_ctx *ctx, const sbr_scene *scene, const float *tx, int
         // the candidate list borrows the dedup table, which is cleared after this step
         df.cand = reinterpret_cast<float4 *>(paths->table);
         df.cand_cap = paths->table_slots * 5 / 8;
+        df.tiled_n = a.tiled_n;
         Range r("sbr_launch: diffraction");
         SBR_CUDA(launch_diffract(df, ctx->num_sms, ctx->stream));
     }

@@ -15,6 +15,7 @@
 // Candidate wedges come from a BVH over the wedge segments, each node box grown by
 // tan(cone) times the largest foot of its corners on the ray: every point of the box
 // inside the ray cone then lies within that margin of the ray (see cone_box).
+#include "lattice_order.cuh"
 #include "sbr_device.cuh"
 
 namespace sbr {
@@ -102,7 +103,8 @@ __global__ void __launch_bounds__(128) diffract_candidates(DiffractArgs A) {
         const long long i = base + lane;
         bool done = i >= total, tail = false;
         const int txi = done ? 0 : (int)(i / A.nrays_per_tx);
-        const int ray = done ? 0 : (int)(A.ray_begin + (i - (long long)txi * A.nrays_per_tx));
+        const int local = done ? 0 : (int)(i - (long long)txi * A.nrays_per_tx);
+        const int ray = A.tiled_n > 0 ? tiled_ray(local, A.tiled_n) : (int)A.ray_begin + local;
         const float3 o = f3(__ldg(A.tx + txi));
         const float3 d = f3(__ldg(A.dirs + ray));
         const RayPre r = make_ray(o, d);

@@ -284,6 +284,7 @@ struct DiffractArgs {
     long long *counters;
     float4 *cand;             // candidate (ray, wedge) list, 2 float4 each (scratch)
     int64_t cand_cap;
+    int tiled_n;              // as TraceArgs::tiled_n: the rays in the order of tiled_ray
 };
 cudaError_t launch_diffract(const DiffractArgs &a, int num_sms, cudaStream_t s);
 
