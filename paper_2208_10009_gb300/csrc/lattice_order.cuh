@@ -24,7 +24,7 @@ __device__ __forceinline__ int layer_prefix(int n, int a) { return (6 * n * a - 
 // are taken in tiles of kTileRows values of p0 by kTileCols of p1, a block of rows at a time:
 // its full tiles, then the rest of its rows (the staircase under the grid's diagonal); every
 // other block runs the other way, so consecutive tiles stay neighbours.
-constexpr int kTileRows = 8, kTileCols = 4;
+constexpr int kTileRows = 6, kTileCols = 4;
 
 // interior points in rows p0 = 1..x of a face (row p0 holds n - 1 - p0 of them)
 __device__ __forceinline__ int rows_before(int n, int x) { return x * (n - 1) - x * (x + 1) / 2; }
