@@ -97,3 +97,35 @@ def test_largest_lattice_and_top_ray_range(oracle_mod):
     finally:
         ctx.close()
         torch.cuda.empty_cache()
+
+
+def test_largest_lattice_tiled_schedule():
+    """A whole n = 14000 launch (1.96e9 rays) in the tiled schedule against lattice id order:
+    the same segment count and the same face sequence for every 997th ray id, so the
+    schedule's closed form visits every ray once at the largest size too."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    n, order, stride = N_DIV, 2, 997
+    N = 10 * n * n + 2
+    sc, tx, rx = scenes.shoebox_config()
+    ctx = api.Context(0)
+    try:
+        scene = ctx.scene_from(sc)
+        rxs = ctx.rx_upload(rx)
+        paths = ctx.paths_create(1 << 20, 1 << 14)
+        per = (N + stride - 1) // stride
+        out = []
+        for id_order in (False, True):
+            dump = torch.full((1, per, order + 1), -3, dtype=torch.int32, device="cuda")
+            ctx.launch(scene, tx, rxs, paths, n, order, rx_angle_scale=SQ3, sync=True, dump_stride=stride,
+                       dump=dump, records_only=True, id_order=id_order)
+            out.append((dump.cpu().numpy()[0], ctx.launch_stats(paths)))
+        (d1, s1), (d0, s0) = out
+        assert s1["rays"] == s0["rays"] == N
+        assert s1["segments"] == s0["segments"] and s1["records"] == s0["records"]
+        assert np.all(d1[:, 0] >= -1) and np.array_equal(d1, d0)
+        for h in (paths, rxs, scene):
+            h.close()
+    finally:
+        ctx.close()
+        torch.cuda.empty_cache()
