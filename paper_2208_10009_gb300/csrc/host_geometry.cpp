@@ -1,10 +1,17 @@
 // host_geometry.cpp -- host-side construction for the CUDA path: binned-SAH BVH, the
 // equiangular lattice's layer tables (§II.B, Eq. 1-2) and the precise algorithm's
 // sub-ray patterns (§III.B, Fig. 5).
+#include <unistd.h>
+
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <functional>
+#include <mutex>
 #include <numeric>
 #include <system_error>
 #include <thread>
@@ -40,8 +47,81 @@ struct TmpNode {
 };
 
 // Right subtrees of at least this many primitives, within this many levels of the root,
-// are built on threads of their own.
-constexpr int kParallelMin = 512, kParallelDepth = 5;
+// are built by the subtree pool's threads.
+constexpr int kParallelMin = 256, kParallelDepth = 7;
+
+// Worker threads for the builder's subtrees, started on first use and kept for the process
+// (a thread start costs tens of microseconds, a good part of a small tree such as the
+// receivers').  A thread that waits for a subtree runs queued subtrees meanwhile, so waits
+// nested inside subtrees always leave a runnable task to some thread, and a process forked
+// after the pool started (its workers do not exist there) runs every subtree itself.
+class SubtreePool {
+public:
+    static SubtreePool &get() {
+        static SubtreePool pool;
+        return pool;
+    }
+    void submit(std::function<void()> f) {
+        {
+            std::lock_guard<std::mutex> l(m_);
+            q_.push_back(std::move(f));
+        }
+        cv_.notify_one();
+    }
+    // runs one queued subtree; false if none was queued
+    bool run_one() {
+        std::function<void()> f;
+        {
+            std::lock_guard<std::mutex> l(m_);
+            if (q_.empty()) return false;
+            f = std::move(q_.front());
+            q_.pop_front();
+        }
+        f();
+        return true;
+    }
+    ~SubtreePool() {
+        {
+            std::lock_guard<std::mutex> l(m_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto &t : workers_) {
+            if (getpid() == owner_ && t.joinable()) t.join();
+            else if (t.joinable()) t.detach();
+        }
+    }
+
+private:
+    SubtreePool() : owner_(getpid()) {
+        const unsigned hw = std::thread::hardware_concurrency();
+        const unsigned n = hw > 1 ? std::min(hw - 1, 31u) : 0u;
+        try {
+            for (unsigned i = 0; i < n; ++i) workers_.emplace_back([this] { loop(); });
+        } catch (const std::system_error &) {
+            // fewer workers: waiting threads run the subtrees themselves
+        }
+    }
+    void loop() {
+        for (;;) {
+            std::function<void()> f;
+            {
+                std::unique_lock<std::mutex> l(m_);
+                cv_.wait(l, [this] { return stop_ || !q_.empty(); });
+                if (q_.empty()) return;   // stopping
+                f = std::move(q_.front());
+                q_.pop_front();
+            }
+            f();
+        }
+    }
+    std::mutex m_;
+    std::condition_variable cv_;
+    std::deque<std::function<void()>> q_;
+    std::vector<std::thread> workers_;
+    bool stop_ = false;
+    pid_t owner_;
+};
 
 struct Builder {
     const std::vector<float> &lo, &hi;
@@ -55,20 +135,21 @@ struct Builder {
             std::vector<int> &ix, int lm)
         : lo(l), hi(h), cen(c), idx(ix), leaf_max(lm) {}
 
-    // The right subtree [mid, first + count) on a thread of its own: it partitions only its
-    // own range of idx, and its nodes are appended after the left subtree's, in the order
-    // the serial recursion gives them, so the tree and its numbering do not depend on the
-    // threads.  Returns the subtree's root, or -1 if no thread could be started.
+    // The right subtree [mid, first + count) built by the subtree pool while this thread
+    // builds the left one: it partitions only its own range of idx, and its nodes are
+    // appended after the left subtree's, in the order the serial recursion gives them, so
+    // the tree and its numbering do not depend on the threads.  Returns the subtree's root.
     int make_split(int first, int count, int mid, int d, int &l) {
         Builder rb(lo, hi, cen, idx, leaf_max);
-        std::thread th;
-        try {
-            th = std::thread([&rb, mid, first, count, d] { rb.make(mid, first + count - mid, d + 1); });
-        } catch (const std::system_error &) {
-            return -1;
-        }
+        std::atomic<bool> done{false};
+        SubtreePool &pool = SubtreePool::get();
+        pool.submit([&rb, &done, mid, first, count, d] {
+            rb.make(mid, first + count - mid, d + 1);
+            done.store(true, std::memory_order_release);
+        });
         l = make(first, mid - first, d + 1);
-        th.join();
+        while (!done.load(std::memory_order_acquire))
+            if (!pool.run_one()) std::this_thread::yield();
         const int off = (int)nodes.size();
         for (TmpNode t : rb.nodes) {
             if (t.left >= 0) {
@@ -181,8 +262,9 @@ struct Builder {
             if (mid == first || mid == first + count) mid = first + count / 2;
         }
         int l = -1, r = -1;
-        if (count >= kParallelMin && d <= kParallelDepth) r = make_split(first, count, mid, d, l);
-        if (r < 0) {
+        if (count >= kParallelMin && d <= kParallelDepth) {
+            r = make_split(first, count, mid, d, l);
+        } else {
             l = make(first, mid - first, d + 1);
             r = make(mid, first + count - mid, d + 1);
         }
